@@ -1,0 +1,141 @@
+"""CPU oracle for exact k-smallest selection — TEST INFRASTRUCTURE.
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it, and
+it shares no code with the CUDA path.
+
+The C file next to this one (``oracle.c``) states what is computed: all n pairs
+(key, position) sorted once under the key type's value order (integers by
+value, floats by IEEE 754 totalOrder), first k taken (paper, Section 2 for the
+(value, position) tie-break, Section 4 for the problem, Appendix A for the
+multisequence split positions).  This module only loads that library and moves
+numpy arrays in and out of it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH, build as _build
+
+DTYPE_CODES = {"u32": 0, "i32": 1, "f32": 2, "bf16": 3, "u64": 4}
+NP_STORAGE = {"u32": np.uint32, "i32": np.uint32, "f32": np.uint32,
+              "bf16": np.uint16, "u64": np.uint64}
+
+
+def _bits(keys: np.ndarray, dtype: str) -> np.ndarray:
+    """Raw key bits as a contiguous unsigned array of the key's width."""
+    store = NP_STORAGE[dtype]
+    a = np.ascontiguousarray(keys)
+    if a.dtype.itemsize != np.dtype(store).itemsize:
+        raise ValueError(f"{dtype} keys need {np.dtype(store).itemsize}-byte items")
+    return a.view(store)
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Oracle:
+    """The oracle library at ``path`` with numpy-level entry points."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        u64, u32, i32 = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+        vp = ctypes.c_void_p
+        lib.oracle_key_cmp.argtypes = [i32, u64, u64]
+        lib.oracle_key_cmp.restype = i32
+        lib.oracle_sort_order.argtypes = [vp, u64, i32, vp]
+        lib.oracle_sort_order.restype = i32
+        lib.oracle_select.argtypes = [vp, u64, i32, u64, vp, vp]
+        lib.oracle_select.restype = i32
+        lib.oracle_select_runs.argtypes = [vp, vp, u32, u64, vp, vp, vp]
+        lib.oracle_select_runs.restype = i32
+        lib.oracle_select_batched.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp]
+        lib.oracle_select_batched.restype = i32
+        self.lib = lib
+        self.path = path
+
+    def key_cmp(self, dtype: str, a: int, b: int) -> int:
+        """-1/0/+1 comparison of two raw key bit patterns."""
+        return self.lib.oracle_key_cmp(DTYPE_CODES[dtype], int(a), int(b))
+
+    def sort_order(self, keys: np.ndarray, dtype: str) -> np.ndarray:
+        """Permutation listing positions in ascending (key, position) order."""
+        k = _bits(keys, dtype)
+        perm = np.empty(k.size, np.uint32)
+        if self.lib.oracle_sort_order(_ptr(k), k.size, DTYPE_CODES[dtype], _ptr(perm)) != 0:
+            raise ValueError("oracle_sort_order rejected its arguments")
+        return perm
+
+    def select(self, keys: np.ndarray, dtype: str, k: int):
+        """(sel_idx ascending by pair order, kth_idx) of the k smallest pairs."""
+        a = _bits(keys, dtype)
+        sel = np.empty(max(int(k), 1), np.uint32)
+        kth = np.zeros(1, np.uint32)
+        if self.lib.oracle_select(_ptr(a), a.size, DTYPE_CODES[dtype], int(k),
+                                  _ptr(sel), _ptr(kth)) != 0:
+            raise ValueError("oracle_select rejected its arguments")
+        return sel[: int(k)], int(kth[0])
+
+    def select_runs(self, keys: np.ndarray, run_off: np.ndarray, k: int):
+        """(split[p], kth_run, kth_pos) for multisequence selection of rank k."""
+        a = _bits(keys, "u64")
+        off = np.ascontiguousarray(run_off, dtype=np.uint64)
+        p = off.size - 1
+        split = np.zeros(p, np.uint64)
+        kr = np.zeros(1, np.uint32)
+        kp = np.zeros(1, np.uint64)
+        if self.lib.oracle_select_runs(_ptr(a), _ptr(off), p, int(k), _ptr(split),
+                                       _ptr(kr), _ptr(kp)) != 0:
+            raise ValueError("oracle_select_runs rejected its arguments")
+        return split, int(kr[0]), int(kp[0])
+
+    def select_batched(self, keys: np.ndarray, row_off: np.ndarray, row_k: np.ndarray,
+                       dtype: str):
+        """(sel_idx concatenated per row, out_off, kth_idx[rows]); indices row-local."""
+        a = _bits(keys, dtype)
+        off = np.ascontiguousarray(row_off, dtype=np.uint64)
+        rk = np.ascontiguousarray(row_k, dtype=np.uint32)
+        rows = rk.size
+        out_off = np.zeros(rows + 1, np.uint64)
+        out_off[1:] = np.cumsum(rk.astype(np.uint64))
+        sel = np.empty(max(int(out_off[-1]), 1), np.uint32)
+        kth = np.zeros(max(rows, 1), np.uint32)
+        if self.lib.oracle_select_batched(_ptr(a), _ptr(off), _ptr(rk), rows,
+                                          DTYPE_CODES[dtype], _ptr(out_off), _ptr(sel),
+                                          _ptr(kth)) != 0:
+            raise ValueError("oracle_select_batched rejected its arguments")
+        return sel[: int(out_off[-1])], out_off, kth[:rows]
+
+
+_default = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle(_build())
+    return _default
+
+
+def key_cmp(dtype, a, b):
+    return default().key_cmp(dtype, a, b)
+
+
+def sort_order(keys, dtype):
+    return default().sort_order(keys, dtype)
+
+
+def select(keys, dtype, k):
+    return default().select(keys, dtype, k)
+
+
+def select_runs(keys, run_off, k):
+    return default().select_runs(keys, run_off, k)
+
+
+def select_batched(keys, row_off, row_k, dtype):
+    return default().select_batched(keys, row_off, row_k, dtype)

@@ -1,0 +1,35 @@
+"""Compiles the C oracle into a shared library next to its source.
+
+Test infrastructure: builds the checker only.  Plain gcc, no CUDA, no flags that
+depend on the host CPU, so the same source builds on x86_64 and aarch64.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "oracle.c")
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+CFLAGS = ["-O2", "-std=c99", "-Wall", "-Wextra", "-fPIC", "-shared"]
+
+
+def compile_source(src: str, out: str) -> str:
+    """gcc one oracle source file into a shared library at ``out``."""
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", *CFLAGS, "-I", HERE, src, "-o", tmp], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    fresh = os.path.exists(LIB_PATH) and all(
+        os.path.getmtime(LIB_PATH) >= os.path.getmtime(os.path.join(HERE, f))
+        for f in ("oracle.c", "oracle.h"))
+    if force or not fresh:
+        compile_source(SRC, LIB_PATH)
+    return LIB_PATH
+
+
+if __name__ == "__main__":
+    print(build(force=True))

@@ -1,0 +1,83 @@
+/*
+ * oracle.h — CPU oracle for exact k-smallest selection (TEST INFRASTRUCTURE).
+ *
+ * This header and oracle.c are test infrastructure.  Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark may load them.  The
+ * product path (the CUDA library) shares no code, header, table or constant
+ * with this directory, and neither side includes the other.
+ *
+ * What it computes (paper, Section 2 "Preliminaries" and Section 4):
+ *   - the objects are made unique by replacing value v of object x by the
+ *     pair (v, x), x = the object's position in the input (Section 2);
+ *   - selection returns the objects of rank <= k, i.e. the k smallest pairs,
+ *     and the object of rank k (Section 4, problem statement; Algorithm
+ *     "select" returns the object of rank k);
+ *   - multisequence selection returns, for p sorted sequences, how many of
+ *     each sequence lie among the k smallest of the union (Section 4.2 and
+ *     Appendix A, Algorithm msSelect), ties ordered by (run, position).
+ *
+ * Value order per key type:
+ *   ORC_U32, ORC_U64 : unsigned integer order;
+ *   ORC_I32          : two's-complement signed order;
+ *   ORC_F32, ORC_BF16: IEEE 754-2008 totalOrder (clause 5.10) on the bit
+ *                      pattern: every negative pattern precedes every positive
+ *                      one; among positives a larger magnitude field is larger;
+ *                      among negatives a larger magnitude field is smaller.
+ *                      Hence -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN.
+ *
+ * Method: build all n pairs, sort them once with a comparator written from the
+ * order above (C library qsort), take the first k.  Plain and slow on purpose.
+ */
+#ifndef TOPK_ORACLE_H
+#define TOPK_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_U32 = 0, ORC_I32 = 1, ORC_F32 = 2, ORC_BF16 = 3, ORC_U64 = 4 };
+
+/* Key width in bytes of a dtype code, 0 if unknown. */
+int oracle_key_bytes(int dtype);
+
+/* Compare two raw key bit patterns (zero-extended into 64 bits) under the
+ * value order of `dtype`.  Returns -1, 0 or +1. */
+int oracle_key_cmp(int dtype, uint64_t a, uint64_t b);
+
+/* Full ascending order of the n pairs (keys[i], i): perm[r] = index of the
+ * pair of rank r+1.  keys holds n keys of `dtype` in host memory.
+ * Returns 0, or -1 on bad arguments / allocation failure. */
+int oracle_sort_order(const void *keys, uint64_t n, int dtype, uint32_t *perm);
+
+/* The k smallest pairs.  sel_idx receives their k indices in ascending pair
+ * order; *kth_idx the index of the pair of rank k.  Needs 1 <= k <= n,
+ * n < 2^32.  Returns 0, or -1 on bad arguments. */
+int oracle_select(const void *keys, uint64_t n, int dtype, uint64_t k,
+                  uint32_t *sel_idx, uint32_t *kth_idx);
+
+/* Multisequence selection over p runs stored back to back in `keys`
+ * (u64 keys; run r is keys[run_off[r] .. run_off[r+1]) ).  Pairs are ordered
+ * by (key, run, position), i.e. by (key, concatenated index).  split[r]
+ * receives the number of the k smallest pairs that lie in run r; *kth_run and
+ * *kth_pos the run and position of the pair of rank k.  The runs need not be
+ * sorted for this definition; when they are, split[r] is the prefix of run r
+ * that is selected.  Needs 1 <= k <= total, total < 2^32.  Returns 0 or -1. */
+int oracle_select_runs(const uint64_t *keys, const uint64_t *run_off, uint32_t p,
+                       uint64_t k, uint64_t *split, uint32_t *kth_run,
+                       uint64_t *kth_pos);
+
+/* Independent selections over `rows` rows stored back to back:
+ * row i is keys[row_off[i] .. row_off[i+1]) with its own k = row_k[i].
+ * The selected indices (row-local, ascending pair order) of row i go to
+ * sel_idx[out_off[i] .. out_off[i] + row_k[i]); kth_idx[i] gets row i's
+ * rank-k index.  Returns 0 or -1. */
+int oracle_select_batched(const void *keys, const uint64_t *row_off,
+                          const uint32_t *row_k, uint32_t rows, int dtype,
+                          const uint64_t *out_off, uint32_t *sel_idx,
+                          uint32_t *kth_idx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

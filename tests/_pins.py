@@ -1,0 +1,264 @@
+"""Checks that pin the CPU oracle to things other than itself.
+
+Each check returns a list of failure strings (empty = pass), so the same
+checks run both against the real oracle (tests/test_oracle_pins.py) and
+against deliberately broken copies of it (tests/test_oracle_mutants.py), which
+must fail at least one of them.
+
+What pins the oracle (none of it re-types the oracle's comparator):
+  * brute-force rank counting, rank_i = #{j : (v_j, j) < (v_i, i)}, with the
+    value order taken from Python's own int / float comparison (paper,
+    Section 2: unique order by (value, position));
+  * exhaustive small inputs over 3-letter alphabets, which force ties;
+  * special cases that are library routines: k = 1 is min(), k = n is a
+    stable sort, integer selection is numpy's stable argsort, heapq.nsmallest;
+  * IEEE 754 totalOrder on a hand-written fixture (tests/golden) and on all
+    2^16 bf16 patterns, via a float-semantics order key;
+  * multisequence selection against heapq.merge of the runs (Appendix A).
+"""
+from __future__ import annotations
+
+import heapq
+import itertools
+import math
+import os
+import struct
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+# ------------------------------------------------------------- value orders
+
+def f32_value_key(bits: int):
+    """Sort key for a binary32 pattern under totalOrder, built on Python float
+    semantics (not on bit tricks): NaNs by sign then payload, numbers by value,
+    and -0 before +0."""
+    bits &= 0xFFFFFFFF
+    f = struct.unpack("<f", struct.pack("<I", bits))[0]
+    neg = bits >> 31
+    if math.isnan(f):
+        payload = bits & 0x7FFFFF
+        return (0, -payload, 0) if neg else (2, payload, 0)
+    return (1, f, 0 if math.copysign(1.0, f) < 0 else 1)
+
+
+def bf16_value_key(bits: int):
+    return f32_value_key((bits & 0xFFFF) << 16)
+
+
+def i32_value_key(bits: int):
+    bits &= 0xFFFFFFFF
+    return bits - (1 << 32) if bits >> 31 else bits
+
+
+def uint_value_key(bits: int):
+    return int(bits)
+
+
+VALUE_KEY = {"u32": uint_value_key, "u64": uint_value_key, "i32": i32_value_key,
+             "f32": f32_value_key, "bf16": bf16_value_key}
+STORE = {"u32": np.uint32, "i32": np.uint32, "f32": np.uint32, "bf16": np.uint16,
+         "u64": np.uint64}
+
+
+def brute_force_ranks(keys, dtype):
+    vk = VALUE_KEY[dtype]
+    pairs = [(vk(int(x)), i) for i, x in enumerate(keys)]
+    return [sum(1 for q in pairs if q < p) for p in pairs]
+
+
+def expected_by_brute_force(keys, dtype, k):
+    ranks = brute_force_ranks(keys, dtype)
+    order = sorted(range(len(keys)), key=lambda i: ranks[i])
+    return order[:k], order[k - 1]
+
+
+# ------------------------------------------------------------------ checks
+
+def check_brute_force(orc, seed=0, sizes=(1, 2, 3, 5, 8, 13, 31, 64)):
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for dtype in ("u32", "i32", "f32", "bf16", "u64"):
+        for n in sizes:
+            if dtype in ("f32", "bf16"):
+                # small value pool with specials so ties and -0/+0/NaN occur
+                pool = [0x00000000, 0x80000000, 0x3F800000, 0xBF800000, 0x7F800000,
+                        0xFF800000, 0x7FC00000, 0xFFC00000, 0x00000001, 0x80000001]
+                if dtype == "bf16":
+                    pool = [p >> 16 for p in pool] + [0x0001, 0x8001]
+                keys = np.array(g.choice(pool, size=n), dtype=STORE[dtype])
+            elif dtype == "u64":
+                pool = [0, 1, 1 << 32, (1 << 63) - 1, 1 << 63, (1 << 64) - 1]
+                keys = np.array([pool[i] for i in g.integers(0, len(pool), size=n)],
+                                dtype=np.uint64)
+            else:
+                # the same pool for u32 and i32: the two orders differ on it
+                pool = [0, 1, 2, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFE, 0xFFFFFFFF]
+                keys = np.array(g.choice(pool, size=n), dtype=np.uint32)
+            for k in range(1, n + 1):
+                want_sel, want_kth = expected_by_brute_force(keys, dtype, k)
+                sel, kth = orc.select(keys, dtype, k)
+                if list(sel) != want_sel or kth != want_kth:
+                    fails.append(f"brute force {dtype} n={n} k={k}")
+                    break
+    return fails
+
+
+def check_exhaustive_ties(orc, max_n=7):
+    alphabets = {
+        "u32": [0, 1, 0xFFFFFFFF],
+        "i32": [0xFFFFFFFF, 0, 1],            # -1, 0, 1: differs from unsigned order
+        "f32": [0x80000000, 0x00000000, 0xFFC00000],  # -0, +0, -NaN
+        "bf16": [0x8000, 0x0000, 0x7FC0],     # -0, +0, +NaN
+    }
+    fails = []
+    for dtype, alpha in alphabets.items():
+        for n in range(1, max_n + 1):
+            for combo in itertools.product(alpha, repeat=n):
+                keys = np.array(combo, dtype=STORE[dtype])
+                perm = list(orc.sort_order(keys, dtype))
+                ranks = brute_force_ranks(keys, dtype)
+                want = sorted(range(n), key=lambda i: ranks[i])
+                if perm != want:
+                    fails.append(f"exhaustive {dtype} {combo}")
+                    break
+    return fails
+
+
+def check_library_special_cases(orc, seed=1):
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for dtype in ("u32", "i32", "u64"):
+        n = 5000
+        if dtype == "u64":
+            keys = g.integers(0, 1000, size=n, dtype=np.uint64) * np.uint64(1 << 50)
+        else:
+            keys = g.integers(0, 1000, size=n, dtype=np.uint64).astype(np.uint32) * np.uint32(4194301)
+        vk = VALUE_KEY[dtype]
+        as_int = [vk(int(x)) for x in keys]
+        # k = 1: min over pairs
+        sel, kth = orc.select(keys, dtype, 1)
+        mn = min(zip(as_int, range(n)))
+        if kth != mn[1] or list(sel) != [mn[1]]:
+            fails.append(f"k=1 vs min {dtype}")
+        # k = n: Python's stable sort by value
+        stable = sorted(range(n), key=lambda i: as_int[i])
+        sel, kth = orc.select(keys, dtype, n)
+        if list(sel) != stable or kth != stable[-1]:
+            fails.append(f"k=n vs stable sort {dtype}")
+        # numpy stable argsort on the signed/unsigned values
+        typed = keys.view(np.int32) if dtype == "i32" else keys
+        ref = np.argsort(typed, kind="stable")
+        for k in (1, 7, 100, 2500, n):
+            sel, kth = orc.select(keys, dtype, k)
+            if not np.array_equal(sel, ref[:k]) or kth != ref[k - 1]:
+                fails.append(f"numpy stable argsort {dtype} k={k}")
+        # heapq.nsmallest on (value, position)
+        for k in (3, 50):
+            want = [i for _, i in heapq.nsmallest(k, zip(as_int, range(n)))]
+            sel, _ = orc.select(keys, dtype, k)
+            if list(sel) != want:
+                fails.append(f"heapq.nsmallest {dtype} k={k}")
+    # float without NaN and without -0: numpy's stable argsort is totalOrder
+    x = g.standard_normal(4000).astype(np.float32)
+    x[::7] = x[3]                          # ties
+    x[x == 0] = 1.0
+    ref = np.argsort(x, kind="stable")
+    for k in (1, 10, 2000, 4000):
+        sel, kth = orc.select(x.view(np.uint32), "f32", k)
+        if not np.array_equal(sel, ref[:k]) or kth != ref[k - 1]:
+            fails.append(f"numpy stable argsort f32 k={k}")
+    return fails
+
+
+def load_golden_f32_order():
+    out = []
+    with open(os.path.join(GOLDEN, "f32_total_order.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                out.append(int(line, 16))
+    return out
+
+
+def check_total_order_fixture(orc, seed=2):
+    fails = []
+    golden = load_golden_f32_order()
+    g = np.random.Generator(np.random.Philox(seed))
+    for trial in range(5):
+        shuffled = np.array(golden, dtype=np.uint32)[g.permutation(len(golden))]
+        perm = orc.sort_order(shuffled, "f32")
+        if [int(v) for v in shuffled[perm]] != golden:
+            fails.append("f32 totalOrder fixture")
+            break
+    # the fixture also agrees with the float-semantics key (self-consistency)
+    if sorted(golden, key=f32_value_key) != golden:
+        fails.append("fixture vs float key")
+    return fails
+
+
+def check_bf16_exhaustive(orc):
+    allbits = np.arange(1 << 16, dtype=np.uint32).astype(np.uint16)
+    perm = orc.sort_order(allbits, "bf16")
+    want = sorted(range(1 << 16), key=lambda b: (bf16_value_key(b), b))
+    return [] if list(perm) == want else ["bf16 exhaustive totalOrder"]
+
+
+def merged_runs_reference(keys, off, k):
+    runs = []
+    for r in range(len(off) - 1):
+        a, b = int(off[r]), int(off[r + 1])
+        runs.append([(int(keys[a + j]), r, j) for j in range(b - a)])
+    merged = list(itertools.islice(heapq.merge(*runs), k))
+    split = [0] * (len(off) - 1)
+    for _, r, _j in merged:
+        split[r] += 1
+    return split, merged[-1][1], merged[-1][2]
+
+
+def check_runs_vs_merge(orc, seed=3):
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for trial in range(40):
+        p = int(g.integers(1, 9))
+        lens = g.integers(0, 12, size=p)
+        if lens.sum() == 0:
+            lens[0] = 1
+        off = np.zeros(p + 1, np.uint64)
+        off[1:] = np.cumsum(lens)
+        keys = (g.integers(0, 5, size=int(off[-1])) * 3).astype(np.uint64)
+        for r in range(p):
+            keys[int(off[r]):int(off[r + 1])].sort()
+        total = int(off[-1])
+        for k in range(1, total + 1):
+            split, kr, kp = orc.select_runs(keys, off, k)
+            ws, wr, wp = merged_runs_reference(keys, off, k)
+            if list(split) != ws or (kr, kp) != (wr, wp):
+                fails.append(f"runs vs heapq.merge trial={trial} k={k}")
+                return fails
+    return fails
+
+
+def check_batched_rows(orc, seed=4):
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    lens = g.integers(1, 40, size=9)
+    off = np.zeros(10, np.uint64)
+    off[1:] = np.cumsum(lens)
+    keys = g.integers(0, 6, size=int(off[-1])).astype(np.uint32)
+    ks = np.array([int(g.integers(1, l + 1)) for l in lens], np.uint32)
+    sel, out_off, kth = orc.select_batched(keys, off, ks, "u32")
+    for i in range(9):
+        row = keys[int(off[i]):int(off[i + 1])]
+        want_sel, want_kth = expected_by_brute_force(row, "u32", int(ks[i]))
+        got = list(sel[int(out_off[i]):int(out_off[i + 1])])
+        if got != want_sel or kth[i] != want_kth:
+            fails.append(f"batched row {i}")
+    return fails
+
+
+ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_cases,
+              check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
+              check_batched_rows]

@@ -1,0 +1,188 @@
+/*
+ * topk.h — C ABI of libtopk: exact selection of the k smallest of n keys on
+ * one GB300 GPU (sm_103a).
+ *
+ * Method: sample-based two-pivot selection in the style of distributed
+ * Floyd-Rivest selection (Hübschle-Schneider, Sanders, Müller, "Communication
+ * Efficient Algorithms for Top-k Selection Problems", Section 2, Algorithm
+ * "select"; Section 4.1, Theorem "selectFR"), with the paper's processing
+ * elements mapped to on-device partitions and its collective reductions to
+ * in-kernel block sums; and multisequence selection on locally sorted runs
+ * (Section 4.2; Appendix A, Algorithm msSelect).
+ *
+ * Conventions shared by every entry point
+ *  - Order.  Keys are compared by value (u32, u64 unsigned; i32 signed;
+ *    f32 and bf16 by IEEE 754 totalOrder: -NaN < -inf < ... < -0 < +0 < ...
+ *    < +inf < +NaN).  Ties are broken by position, as the paper makes every
+ *    value unique by pairing it with its object (Section 2): the pair
+ *    (key, index) is unique, so the selected set is unique and exact.
+ *  - Memory.  Every pointer whose name starts with d_ is GPU global memory
+ *    owned by the caller; the library never frees it.  Pointers without the
+ *    prefix are host memory.  Inputs are read only.  Outputs must not overlap
+ *    inputs or each other.  Keys may sit at any byte offset that is a multiple
+ *    of the key size; 16-byte-aligned keys take the vectorised path.
+ *  - Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Calls enqueue work and return without waiting.
+ *  - Errors.  Argument errors are returned at once and enqueue nothing.
+ *    Errors found on the device are latched in the context and returned by
+ *    topk_status_sync().  TOPK_ECUDA reports a failed CUDA runtime call.
+ *  - Output order.  The k selected pairs are written in no particular order.
+ *  - Threads.  A context is used by one host thread at a time.
+ */
+#ifndef TOPK_H
+#define TOPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TOPK_U32 = 0,  /* uint32_t */
+    TOPK_I32 = 1,  /* int32_t */
+    TOPK_F32 = 2,  /* IEEE binary32 */
+    TOPK_BF16 = 3, /* bfloat16 (upper half of a binary32) */
+    TOPK_U64 = 4   /* uint64_t */
+} topk_dtype;
+
+typedef enum {
+    TOPK_OK = 0,
+    TOPK_EINVAL = 1,     /* bad argument; nothing was enqueued */
+    TOPK_ENOMEM = 2,     /* device scratch could not be allocated */
+    TOPK_ECUDA = 3,      /* a CUDA runtime call failed */
+    TOPK_ETIMEOUT = 4,   /* a bounded device wait gave up */
+    TOPK_EBUDGET = 5,    /* serving: request exceeds the HBM budget */
+    TOPK_EBUSY = 6,      /* serving: no free slot / queue full */
+    TOPK_EINTERNAL = 7   /* recursion did not converge within its level limit */
+} topk_status;
+
+/* Flags for topk_params.flags. */
+#define TOPK_FLAG_CHECK_SORTED 0x1u  /* sorted runs: verify order, else EINVAL */
+#define TOPK_FLAG_RAW_DELTA 0x2u     /* use delta_factor alone as the pivot
+                                        margin (testing: provokes pivot
+                                        failures, results stay exact) */
+#define TOPK_FLAG_TINY_CAND 0x4u     /* testing: minimal candidate buffers so
+                                        the overflow paths run */
+
+/* Tuning knobs; a zero field means "choose automatically".  None of them can
+ * change a result, only the time taken. */
+typedef struct {
+    uint64_t seed;             /* Philox4x32-10 key for the sampler */
+    uint32_t partitions;       /* p: sampling partitions (the paper's PEs) */
+    uint32_t sample_size;      /* s: sample drawn per recursion level */
+    uint32_t buckets;          /* reserved; the method uses 3 (a, b, c) */
+    uint32_t finish_threshold; /* T: at most this many candidates are
+                                  finished by one thread block */
+    float delta_factor;        /* z: pivot margin in standard deviations */
+    uint32_t flags;            /* TOPK_FLAG_* */
+} topk_params;
+
+/* Counters of the last completed call on a context (valid after
+ * topk_status_sync). */
+typedef struct {
+    uint32_t levels_grid;      /* recursion levels run by the whole grid */
+    uint32_t levels_block;     /* recursion levels run inside one block */
+    uint32_t pivot_failures;   /* levels whose bracket missed rank k */
+    uint32_t overflows;        /* levels whose candidates exceeded the buffer */
+    uint64_t first_candidates; /* |b| after the first level */
+    uint64_t sample_kept;      /* sample size of the first level */
+} topk_stats;
+
+typedef struct topk_ctx topk_ctx;
+
+/* Creates a context on `device`: owns device scratch (grown on demand) and
+ * the latched device status.  Returns TOPK_EINVAL for a bad device. */
+topk_status topk_ctx_create(topk_ctx **out, int device);
+
+/* Waits for the context's work, frees its scratch and the context. */
+void topk_ctx_destroy(topk_ctx *ctx);
+
+/* Pre-allocates scratch for selections of up to n keys of `dtype`, so that
+ * later calls of that size allocate nothing (needed before stream capture).
+ * Synchronous. */
+topk_status topk_ctx_reserve(topk_ctx *ctx, uint64_t n, topk_dtype dtype);
+
+/* Selection of the k smallest of n unsorted keys (Section 2, Algorithm
+ * "select"; Section 4.1).
+ *   d_keys     n keys of `dtype`, contiguous.
+ *   n, k       1 <= k <= n < 2^32.
+ *   d_out_keys k keys of `dtype`: the selected keys, bit-identical to the
+ *              input (any order).
+ *   d_out_idx  k uint32: their positions in d_keys (same order as keys).
+ *   d_kth_key  1 key of `dtype`: the key of rank k (the largest selected).
+ *   d_kth_idx  1 uint32: its position.
+ *   params     NULL or tuning knobs.
+ *   stream     cudaStream_t.
+ * Returns TOPK_EINVAL for k == 0, k > n, n >= 2^32, a NULL pointer, an
+ * unknown dtype or keys not aligned to their size. */
+topk_status topk_select(topk_ctx *ctx, const void *d_keys, uint64_t n, uint64_t k,
+                        topk_dtype dtype, void *d_out_keys, uint32_t *d_out_idx,
+                        void *d_kth_key, uint32_t *d_kth_idx,
+                        const topk_params *params, void *stream);
+
+/* Multisequence selection over p locally sorted runs (Section 4.2;
+ * Appendix A, Algorithm msSelect, with several pivots per round as in
+ * Section 4.3 "Multiple Concurrent Trials").
+ *   d_keys     uint64 keys of all runs back to back (dtype must be TOPK_U64).
+ *   d_run_off  p + 1 uint64 offsets: run r is d_keys[off[r] .. off[r+1]),
+ *              non-decreasing within the run; off[0] = 0.
+ *   p          number of runs, >= 1.
+ *   k          1 <= k <= off[p] < 2^40.
+ *   d_split    p uint64: how many of the k smallest lie in run r; the first
+ *              d_split[r] keys of run r are selected.
+ *   d_kth_key, d_kth_run, d_kth_pos  the pair of rank k: its key, run and
+ *              position inside the run.
+ * Ties are ordered by (run, position).  TOPK_FLAG_CHECK_SORTED makes the
+ * device verify the runs' order and report TOPK_EINVAL from
+ * topk_status_sync() when a run is not sorted. */
+topk_status topk_select_sorted_runs(topk_ctx *ctx, const void *d_keys,
+                                    const uint64_t *d_run_off, uint32_t p, uint64_t k,
+                                    topk_dtype dtype, uint64_t *d_split,
+                                    void *d_kth_key, uint32_t *d_kth_run,
+                                    uint64_t *d_kth_pos, const topk_params *params,
+                                    void *stream);
+
+/* Many independent selections in one persistent launch (no counterpart in the
+ * paper: it is the selection of Section 2 run once per row).
+ *   d_keys     all rows back to back, `dtype`.
+ *   d_row_off  rows + 1 uint64 offsets (row i = keys[off[i] .. off[i+1])).
+ *   d_row_k    rows uint32: k of each row, 1 <= k_i <= row length.
+ *   rows       >= 1.
+ *   d_out_keys, d_out_idx  per row k_i keys / row-local uint32 positions at
+ *              [d_out_off[i], d_out_off[i] + k_i).
+ *   d_out_off  rows + 1 uint64 output offsets (caller computes the prefix sum
+ *              of d_row_k).
+ *   d_kth_keys, d_kth_idx  rows entries: each row's key and position of
+ *              rank k_i.
+ * Row lengths must be < 2^32.  Rows with bad k are reported by
+ * topk_status_sync() as TOPK_EINVAL (their outputs are left untouched). */
+topk_status topk_select_batched(topk_ctx *ctx, const void *d_keys,
+                                const uint64_t *d_row_off, const uint32_t *d_row_k,
+                                uint32_t rows, topk_dtype dtype, void *d_out_keys,
+                                uint32_t *d_out_idx, const uint64_t *d_out_off,
+                                void *d_kth_keys, uint32_t *d_kth_idx,
+                                const topk_params *params, void *stream);
+
+/* Synchronises `stream`, then returns and clears the first error latched by
+ * device code of this context (TOPK_OK if none). */
+topk_status topk_status_sync(topk_ctx *ctx, void *stream);
+
+/* Counters of the last selection (call after topk_status_sync). */
+topk_status topk_last_stats(topk_ctx *ctx, topk_stats *out);
+
+/* Human-readable name of a status code (static string). */
+const char *topk_status_string(topk_status s);
+
+/* Diagnostic: fills d_out[4*i .. 4*i+3] with Philox4x32-10 (Salmon, Moraes,
+ * Dror, Shaw, SC'11) of counter {c0 + i, c1, c2, c3} and key {k0, k1}, for
+ * i < count, on the device.  Lets a test pin the sampler's generator to the
+ * published known-answer vectors.  Synchronous. */
+topk_status topk_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                              uint32_t k0, uint32_t k1, uint32_t *d_out,
+                              uint32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,201 @@
+"""Python binding of libtopk (include/topk.h): exact k-smallest selection on a
+GB300 GPU.
+
+Argument marshalling only.  Every step of the selection runs in the library's
+CUDA kernels; PyTorch provides device memory and streams.  There is no CPU
+fallback: if the compiled library is missing, every call raises.
+
+The C names are kept: ``topk_select``, ``topk_select_sorted_runs``,
+``topk_select_batched``, ``topk_status_sync`` and the ``topk_serve_*`` family,
+each taking a :class:`Context` (or server) first and torch tensors for the
+device buffers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtopk.so")
+
+TOPK_U32, TOPK_I32, TOPK_F32, TOPK_BF16, TOPK_U64 = 0, 1, 2, 3, 4
+TOPK_OK, TOPK_EINVAL, TOPK_ENOMEM, TOPK_ECUDA, TOPK_ETIMEOUT = 0, 1, 2, 3, 4
+TOPK_EBUDGET, TOPK_EBUSY, TOPK_EINTERNAL = 5, 6, 7
+TOPK_FLAG_CHECK_SORTED = 0x1
+TOPK_FLAG_RAW_DELTA = 0x2
+TOPK_FLAG_TINY_CAND = 0x4
+
+DTYPE_NAMES = {TOPK_U32: "u32", TOPK_I32: "i32", TOPK_F32: "f32", TOPK_BF16: "bf16",
+               TOPK_U64: "u64"}
+
+
+class TopkError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})" if what else status_string(status))
+
+
+class topk_params(ctypes.Structure):
+    _fields_ = [("seed", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
+                ("sample_size", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
+                ("finish_threshold", ctypes.c_uint32), ("delta_factor", ctypes.c_float),
+                ("flags", ctypes.c_uint32)]
+
+
+class topk_stats(ctypes.Structure):
+    _fields_ = [("levels_grid", ctypes.c_uint32), ("levels_block", ctypes.c_uint32),
+                ("pivot_failures", ctypes.c_uint32), ("overflows", ctypes.c_uint32),
+                ("first_candidates", ctypes.c_uint64), ("sample_kept", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads libtopk.so (raises if it was not built: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtopk.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    st = ctypes.c_int
+    lib.topk_ctx_create.argtypes = [ctypes.POINTER(vp), i32]
+    lib.topk_ctx_create.restype = st
+    lib.topk_ctx_destroy.argtypes = [vp]
+    lib.topk_ctx_destroy.restype = None
+    lib.topk_ctx_reserve.argtypes = [vp, u64, i32]
+    lib.topk_ctx_reserve.restype = st
+    lib.topk_select.argtypes = [vp, vp, u64, u64, i32, vp, vp, vp, vp, vp, vp]
+    lib.topk_select.restype = st
+    if hasattr(lib, "topk_select_sorted_runs"):
+        lib.topk_select_sorted_runs.argtypes = [vp, vp, vp, u32, u64, i32, vp, vp, vp, vp, vp, vp]
+        lib.topk_select_sorted_runs.restype = st
+    if hasattr(lib, "topk_select_batched"):
+        lib.topk_select_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp]
+        lib.topk_select_batched.restype = st
+    lib.topk_status_sync.argtypes = [vp, vp]
+    lib.topk_status_sync.restype = st
+    lib.topk_last_stats.argtypes = [vp, ctypes.POINTER(topk_stats)]
+    lib.topk_last_stats.restype = st
+    lib.topk_status_string.argtypes = [st]
+    lib.topk_status_string.restype = ctypes.c_char_p
+    lib.topk_debug_philox.argtypes = [u32, u32, u32, u32, u32, u32, vp, u32]
+    lib.topk_debug_philox.restype = st
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().topk_status_string(status).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _check(status: int, what: str):
+    if status != TOPK_OK:
+        raise TopkError(status, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    m = {torch.uint32: TOPK_U32, torch.int32: TOPK_I32, torch.float32: TOPK_F32,
+         torch.bfloat16: TOPK_BF16, torch.uint64: TOPK_U64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported key dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(seed=0, partitions=0, sample_size=0, finish_threshold=0, delta_factor=0.0,
+                flags=0) -> topk_params:
+    return topk_params(seed, partitions, sample_size, 0, finish_threshold, delta_factor, flags)
+
+
+class Context:
+    """Owns a topk_ctx (device scratch + latched device status)."""
+
+    def __init__(self, device: int = 0):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.topk_ctx_create(ctypes.byref(h), int(device)), "topk_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().topk_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, n: int, dtype: int):
+        _check(load_library().topk_ctx_reserve(self.handle, int(n), int(dtype)), "topk_ctx_reserve")
+
+    def sync(self, stream=None) -> int:
+        """topk_status_sync: waits for the stream, returns the latched status."""
+        return load_library().topk_status_sync(self.handle, _stream_ptr(stream))
+
+    def last_stats(self) -> dict:
+        s = topk_stats()
+        _check(load_library().topk_last_stats(self.handle, ctypes.byref(s)), "topk_last_stats")
+        return {f: getattr(s, f) for f, _ in topk_stats._fields_}
+
+
+def topk_select(ctx: Context, keys, k: int, params: topk_params | None = None, stream=None,
+                out=None, check: bool = True):
+    """k smallest of the 1-D CUDA tensor ``keys``.
+
+    Returns (out_keys[k], out_idx[k] uint32, kth_key[1], kth_idx[1] uint32) as
+    CUDA tensors (outputs allocated here unless ``out`` gives all four).  With
+    ``check`` the call waits and raises on a latched device error."""
+    torch = _torch()
+    if keys.dim() != 1 or not keys.is_cuda:
+        raise ValueError("keys must be a 1-D CUDA tensor")
+    if not keys.is_contiguous():
+        raise ValueError("keys must be contiguous")
+    n = keys.numel()
+    if out is None:
+        kk = max(int(k), 1)
+        out = (torch.empty(kk, dtype=keys.dtype, device=keys.device),
+               torch.empty(kk, dtype=torch.uint32, device=keys.device),
+               torch.empty(1, dtype=keys.dtype, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device))
+    ok, oi, kk_, ki = out
+    st = load_library().topk_select(
+        ctx.handle, _ptr(keys), n, int(k), dtype_code(keys), _ptr(ok), _ptr(oi), _ptr(kk_), _ptr(ki),
+        ctypes.byref(params) if params is not None else None, _stream_ptr(stream))
+    _check(st, "topk_select")
+    if check:
+        _check(ctx.sync(stream), "topk_select (device)")
+    return out
+
+
+def topk_debug_philox(c, key, count: int):
+    """Philox4x32-10 outputs for counters c0+i (i < count), as a uint32 tensor."""
+    torch = _torch()
+    out = torch.empty(4 * count, dtype=torch.uint32, device="cuda")
+    _check(load_library().topk_debug_philox(c[0], c[1], c[2], c[3], key[0], key[1], _ptr(out), count),
+           "topk_debug_philox")
+    return out

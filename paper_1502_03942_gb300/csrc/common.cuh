@@ -1,0 +1,206 @@
+// common.cuh — device building blocks shared by every selection kernel.
+//
+// Key order (paper, Section 2): every object's value v is made unique by
+// pairing it with the object itself; here the object is its position, so the
+// order is on the pair (key', idx), where key' is an order-preserving
+// unsigned image of the key:
+//   u32 -> itself; i32 -> x ^ 0x80000000; u64 -> itself;
+//   f32 / bf16 -> sign-magnitude to unsigned: negative patterns are
+//   complemented, non-negative ones get the sign bit set, which realises IEEE
+//   754 totalOrder on the bit patterns.
+// The pair is packed into one unsigned integer, the "composite":
+//   32-bit keys: (key' << 32) | idx   in a uint64
+//   64-bit keys: (key' << 32) | idx   in an unsigned __int128 (96 bits used)
+// so every comparison of the method is one integer comparison.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace topk {
+
+typedef uint32_t u32;
+typedef uint64_t u64;
+typedef unsigned __int128 u128;
+
+enum : int { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2, DT_BF16 = 3, DT_U64 = 4 };
+
+// ---------------------------------------------------------------- key maps
+
+template <int DT> struct Key;
+
+template <> struct Key<DT_U32> {
+    typedef u32 raw_t;
+    typedef u32 key_t;
+    static constexpr int KW = 32;
+    __host__ __device__ static key_t fwd(raw_t x) { return x; }
+    __host__ __device__ static raw_t inv(key_t k) { return k; }
+};
+template <> struct Key<DT_I32> {
+    typedef u32 raw_t;
+    typedef u32 key_t;
+    static constexpr int KW = 32;
+    __host__ __device__ static key_t fwd(raw_t x) { return x ^ 0x80000000u; }
+    __host__ __device__ static raw_t inv(key_t k) { return k ^ 0x80000000u; }
+};
+template <> struct Key<DT_F32> {
+    typedef u32 raw_t;
+    typedef u32 key_t;
+    static constexpr int KW = 32;
+    // negative: all bits flipped; non-negative: sign bit set
+    __host__ __device__ static key_t fwd(raw_t x) {
+        return x ^ ((u32)((int32_t)x >> 31) | 0x80000000u);
+    }
+    __host__ __device__ static raw_t inv(key_t k) {
+        return k ^ ((u32)((int32_t)~k >> 31) | 0x80000000u);
+    }
+};
+template <> struct Key<DT_BF16> {
+    typedef uint16_t raw_t;
+    typedef u32 key_t; // 16-bit image, zero-extended
+    static constexpr int KW = 32;
+    __host__ __device__ static key_t fwd(raw_t x) {
+        u32 v = x;
+        return v ^ ((v & 0x8000u) ? 0xFFFFu : 0x8000u);
+    }
+    __host__ __device__ static raw_t inv(key_t k) {
+        return (raw_t)(k ^ ((k & 0x8000u) ? 0x8000u : 0xFFFFu));
+    }
+};
+template <> struct Key<DT_U64> {
+    typedef u64 raw_t;
+    typedef u64 key_t;
+    static constexpr int KW = 64;
+    __host__ __device__ static key_t fwd(raw_t x) { return x; }
+    __host__ __device__ static raw_t inv(key_t k) { return k; }
+};
+
+// ------------------------------------------------------------- composites
+
+template <int KW> struct Comp;
+
+template <> struct Comp<32> {
+    typedef u64 t;
+    typedef u32 key_t;
+    static constexpr int DIGITS = 8; // 8-bit digits, most significant first
+    __host__ __device__ static t make(u32 key, u32 idx) { return ((u64)key << 32) | idx; }
+    __host__ __device__ static u32 key(t c) { return (u32)(c >> 32); }
+    __host__ __device__ static u32 idx(t c) { return (u32)c; }
+    __host__ __device__ static t max_value() { return ~(u64)0; }
+    __host__ __device__ static t from128(u128 v) { return (u64)v; }
+    __device__ static u32 digit(t c, int d) { return (u32)(c >> (56 - 8 * d)) & 0xFFu; }
+};
+
+template <> struct Comp<64> {
+    typedef u128 t;
+    typedef u64 key_t;
+    static constexpr int DIGITS = 12;
+    __host__ __device__ static t make(u64 key, u32 idx) { return ((u128)key << 32) | idx; }
+    __host__ __device__ static u64 key(t c) { return (u64)(c >> 32); }
+    __host__ __device__ static u32 idx(t c) { return (u32)c; }
+    __host__ __device__ static t max_value() { return ((u128)1 << 96) - 1; }
+    __host__ __device__ static t from128(u128 v) { return v; }
+    __device__ static u32 digit(t c, int d) { return (u32)(c >> (88 - 8 * d)) & 0xFFu; }
+};
+
+// -------------------------------------------------------- Philox4x32-10
+// Counter-based generator of Salmon, Moraes, Dror and Shaw ("Parallel random
+// numbers: as easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64
+// multiplications whose halves are xored with the other counter words and the
+// round key; the key is bumped by the two Weyl constants between rounds.
+struct Philox4 {
+    u32 v[4];
+};
+
+__host__ __device__ inline Philox4 philox4x32_10(u32 c0, u32 c1, u32 c2, u32 c3, u32 k0, u32 k1) {
+    const u32 M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const u32 W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        u64 p0 = (u64)M0 * c0;
+        u64 p1 = (u64)M1 * c2;
+        u32 hi0 = (u32)(p0 >> 32), lo0 = (u32)p0;
+        u32 hi1 = (u32)(p1 >> 32), lo1 = (u32)p1;
+        u32 n0 = hi1 ^ c1 ^ k0;
+        u32 n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+        k0 += W0;
+        k1 += W1;
+    }
+    Philox4 out;
+    out.v[0] = c0;
+    out.v[1] = c1;
+    out.v[2] = c2;
+    out.v[3] = c3;
+    return out;
+}
+
+// ------------------------------------------------------------ call state
+// One selection in progress.  The window [lo, hi] (composites, inclusive)
+// holds the m_win elements of the current source that are still undecided;
+// the element sought has rank k_rem (1-based) inside the window; out_base
+// outputs are already committed.  A pass splits the window into
+//   a = [lo, pl)   (all selected),  b = [pl, pr]  (candidates),  c = (pr, hi]
+// exactly as Algorithm "select" partitions s into a, b, c (Section 2).
+
+enum : u32 { PH_RUN = 0, PH_FINISH = 1, PH_DONE = 2, PH_ERROR = 3 };
+enum : u32 { SRC_INPUT = 0, SRC_CAND0 = 1, SRC_CAND1 = 2 };
+enum : u32 { ST_OK = 0, ST_EINVAL = 1, ST_ETIMEOUT = 4, ST_EINTERNAL = 7 };
+
+struct alignas(16) SelState {
+    u128 lo, hi;          // window
+    u128 pl, pr;          // pivots of the pending pass
+    u64 m_src;            // elements in the current source array
+    u64 m_win;            // elements of the source inside the window
+    u64 k_rem;            // rank sought inside the window, >= 1
+    u64 out_base;         // outputs committed so far
+    u64 cnt_a, cnt_b;     // pass counters (accumulated by atomics)
+    u64 cap_b;            // capacity of each candidate buffer
+    u64 first_cand;       // statistics
+    u32 level, phase, src, dst;
+    u32 pending;          // a pass ran whose counters are not yet consumed
+    u32 status;           // first device error, ST_*
+    u32 levels_grid, levels_block, failures, overflows;
+    u32 sample_kept, pad0;
+};
+
+// Arguments common to every kernel of one topk_select call.
+struct SelArgs {
+    const void* keys;         // input (raw keys)
+    u64 n, k;
+    void* out_keys;           // k raw keys
+    u32* out_idx;             // k positions
+    void* kth_key;
+    u32* kth_idx;
+    void* cand_key[2];        // candidate buffers: key' (u32 or u64)
+    u32* cand_idx[2];
+    SelState* st;
+    u64 cap_b;
+    u64 seed;
+    u32 parts;                // sampling partitions
+    u32 sample;               // draws per level
+    u32 finish_T;             // single-block finish threshold
+    u32 grid_G;               // grid levels run while m_src > G
+    float z;                  // pivot margin factor
+    u32 flags;
+    u32 aligned;              // input is 16-byte aligned
+    u32* err;                 // context's latched error word
+};
+
+// ---------------------------------------------------------- warp helpers
+
+__device__ __forceinline__ u32 lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ u32 lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+// Streaming 16-byte load (cache-streaming policy: the input is read once per
+// level, so it should not displace the candidate buffers from L2).
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) { return __ldcs(p); }
+
+__device__ __forceinline__ u32 u4get(const uint4& v, int i) {
+    return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
+}
+
+} // namespace topk

@@ -1,0 +1,144 @@
+// ctx.cu — context lifetime, scratch memory, latched device status,
+// statistics and the Philox diagnostic of libtopk.
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace topk {
+
+topk_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TOPK_OK : TOPK_ECUDA; }
+
+int dtype_bytes(topk_dtype dt) {
+    switch (dt) {
+    case TOPK_U32:
+    case TOPK_I32:
+    case TOPK_F32: return 4;
+    case TOPK_BF16: return 2;
+    case TOPK_U64: return 8;
+    default: return 0;
+    }
+}
+
+topk_status ensure_scratch(topk_ctx* ctx, size_t bytes) {
+    if (ctx->scratch.bytes >= bytes) return TOPK_OK;
+    if (ctx->scratch.base) {
+        // work of earlier calls may still read the old block
+        if (cudaDeviceSynchronize() != cudaSuccess) return TOPK_ECUDA;
+        cudaFree(ctx->scratch.base);
+        ctx->scratch.base = nullptr;
+        ctx->scratch.bytes = 0;
+    }
+    size_t want = bytes + bytes / 4; // headroom against repeated growth
+    void* p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return TOPK_ENOMEM;
+        }
+        want = bytes;
+    }
+    ctx->scratch.base = p;
+    ctx->scratch.bytes = want;
+    return TOPK_OK;
+}
+
+__global__ void k_philox(u32 c0, u32 c1, u32 c2, u32 c3, u32 k0, u32 k1, u32* out, u32 count) {
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const Philox4 r = philox4x32_10(c0 + i, c1, c2, c3, k0, k1);
+    out[4 * i + 0] = r.v[0];
+    out[4 * i + 1] = r.v[1];
+    out[4 * i + 2] = r.v[2];
+    out[4 * i + 3] = r.v[3];
+}
+
+} // namespace topk
+
+using namespace topk;
+
+extern "C" {
+
+topk_status topk_ctx_create(topk_ctx** out, int device) {
+    if (!out) return TOPK_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return TOPK_ECUDA;
+    }
+    if (device < 0 || device >= count) return TOPK_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return TOPK_ECUDA;
+    topk_ctx* c = new topk_ctx();
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    // error word, block-done counters (64 slots) and the state, one allocation
+    void* p = nullptr;
+    const size_t bytes = 256 + 64 * sizeof(u32) + 4096;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return TOPK_ENOMEM;
+    }
+    cudaMemset(p, 0, bytes);
+    c->d_err = static_cast<u32*>(p);
+    c->d_counter = reinterpret_cast<u32*>(static_cast<char*>(p) + 256);
+    c->d_state = static_cast<char*>(p) + 256 + 64 * sizeof(u32);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaFree(p);
+        delete c;
+        return TOPK_ECUDA;
+    }
+    *out = c;
+    return TOPK_OK;
+}
+
+void topk_ctx_destroy(topk_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->scratch.base) cudaFree(ctx->scratch.base);
+    if (ctx->d_err) cudaFree(ctx->d_err);
+    delete ctx;
+}
+
+topk_status topk_status_sync(topk_ctx* ctx, void* stream) {
+    if (!ctx) return TOPK_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return TOPK_ECUDA;
+    u32 err = 0;
+    if (cudaMemcpy(&err, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TOPK_ECUDA;
+    if (err != 0) {
+        if (cudaMemset(ctx->d_err, 0, sizeof(u32)) != cudaSuccess) return TOPK_ECUDA;
+        cudaDeviceSynchronize();
+    }
+    return static_cast<topk_status>(err);
+}
+
+const char* topk_status_string(topk_status s) {
+    switch (s) {
+    case TOPK_OK: return "ok";
+    case TOPK_EINVAL: return "invalid argument";
+    case TOPK_ENOMEM: return "out of device memory";
+    case TOPK_ECUDA: return "CUDA runtime error";
+    case TOPK_ETIMEOUT: return "device wait timed out";
+    case TOPK_EBUDGET: return "request exceeds memory budget";
+    case TOPK_EBUSY: return "server busy";
+    case TOPK_EINTERNAL: return "selection did not converge";
+    default: return "unknown status";
+    }
+}
+
+topk_status topk_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                              uint32_t k1, uint32_t* d_out, uint32_t count) {
+    if (!d_out || count == 0) return TOPK_EINVAL;
+    k_philox<<<(count + 255) / 256, 256>>>(c0, c1, c2, c3, k0, k1, d_out, count);
+    if (cudaGetLastError() != cudaSuccess) return TOPK_ECUDA;
+    return cuda_status(cudaDeviceSynchronize());
+}
+
+} // extern "C"

@@ -1,0 +1,610 @@
+// select.cu — topk_select: selection of the k smallest of n unsorted keys
+// (paper, Section 2, Algorithm "select"; Section 4.1, Theorem "selectFR").
+//
+// Launch sequence of one call (all on the caller's stream, no host round
+// trip):
+//   k_plan   (1 block)  level 1: initialise the state, sample, pivots
+//   k_pass   (grid)     level 1: stream the input once, a -> output,
+//                       b -> candidate buffer 0, block sums -> n_a, n_b
+//   k_plan / k_pass     levels 2..L on the candidate buffers (L predicted on
+//                       the host; a level whose state is already small
+//                       returns at once)
+//   k_finish (1 block)  remaining levels inside one block until at most T
+//                       candidates are left, then selects rank k among them,
+//                       writes the rest of the output and the rank-k pair.
+// k = 1 (the base case of Algorithm "select", a global minimum) and k = n
+// (everything selected) take one reduction kernel instead.
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+#include "select_core.cuh"
+
+namespace topk {
+
+constexpr int BLK_NT = 1024;  // planning / finishing block
+constexpr int PASS_NT = 256;  // grid pass block
+constexpr int EXT_NT = 256;   // min / max reduction block
+constexpr u32 MAX_BLOCK_LEVELS = 256;
+
+template <int KW> struct Lim {
+    // sample and finish capacity of one block (128 KiB of composites)
+    static constexpr u32 ELEMS = KW == 32 ? 16384u : 8192u;
+};
+
+template <int KW> struct BlockSmem {
+    typedef typename Comp<KW>::t ct;
+    ct samp[Lim<KW>::ELEMS];
+    RadixSmem<KW, 2> rs2;
+    RadixSmem<KW, 1> rs1;
+    PassSmem<BLK_NT> ps;
+    u32 kept;
+    u32 flag;
+};
+
+__device__ inline void latch(u32* err, u32 code) { atomicCAS(err, 0u, code); }
+
+// All 32 lanes call; returns the slot of this lane's element when `keep`.
+__device__ __forceinline__ u32 warp_append(bool keep, u32* counter) {
+    const u32 bal = __ballot_sync(0xffffffffu, keep);
+    u32 base = 0;
+    if (lane_id() == 0 && bal) base = atomicAdd(counter, (u32)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(bal & lanemask_lt());
+}
+
+template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) {
+    typedef Comp<Key<DT>::KW> C;
+    g->lo = 0;
+    g->hi = (u128)C::max_value();
+    g->pl = 0;
+    g->pr = 0;
+    g->m_src = a.n;
+    g->m_win = a.n;
+    g->k_rem = a.k;
+    g->out_base = 0;
+    g->cnt_a = 0;
+    g->cnt_b = 0;
+    g->cap_b = a.cap_b;
+    g->first_cand = 0;
+    g->level = 0;
+    g->phase = PH_RUN;
+    g->src = SRC_INPUT;
+    g->dst = SRC_CAND0;
+    g->pending = 0;
+    g->status = ST_OK;
+    g->levels_grid = 0;
+    g->levels_block = 0;
+    g->failures = 0;
+    g->overflows = 0;
+    g->sample_kept = 0;
+}
+
+// ------------------------------------------------------------ one pass
+
+template <int NT, int DT, bool INPUT_ONLY = false>
+__device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 step, PassSmem<NT>& ps) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    Sink<DT> sink;
+    sink.out_keys = static_cast<raw_t*>(a.out_keys);
+    sink.out_idx = a.out_idx;
+    sink.out_base = s.out_base;
+    sink.cap_a = s.k_rem;
+    sink.ck = static_cast<key_t*>(a.cand_key[s.dst - 1]);
+    sink.ci = a.cand_idx[s.dst - 1];
+    sink.cap_b = a.cap_b;
+    sink.cnt_a = &a.st->cnt_a;
+    sink.cnt_b = &a.st->cnt_b;
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
+    const bool has_a = pl > lo;
+    if (INPUT_ONLY || s.src == SRC_INPUT) {
+        InputSrc<DT> src{static_cast<const raw_t*>(a.keys), s.m_src, a.aligned != 0};
+        if (has_a) pass_tiles<NT, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else pass_tiles<NT, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+    } else if constexpr (!INPUT_ONLY) {
+        CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
+        if (has_a) pass_tiles<NT, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else pass_tiles<NT, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+    }
+}
+
+// ------------------------------------------------------- pickPivots
+// Samples the window, reads the pivots off the sample and arms the next pass.
+
+template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm, bool grid_level) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    SelState* g = a.st;
+    const SelState s = *g;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
+    u32 kept = 0;
+    if (s.m_win > a.finish_T) {
+        u32 draws = grid_level ? a.sample : (u32)min((u64)a.sample, max((u64)1024, s.m_src / 4));
+        if (s.m_win < s.m_src) { // narrowed window: draw more so enough land inside
+            u64 ratio = s.m_src / (s.m_win ? s.m_win : 1);
+            ratio = ratio < 2 ? 2 : ratio > 64 ? 64 : ratio;
+            draws = (u32)min((u64)draws * ratio / 2, (u64)a.sample * 32);
+        }
+        if (s.src == SRC_INPUT) {
+            InputSrc<DT> src{static_cast<const raw_t*>(a.keys), s.m_src, a.aligned != 0};
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+        } else {
+            CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+        }
+        if (kept > 0) {
+            long long jl, jr;
+            pivot_ranks(kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+            const long long top = (long long)kept - 1;
+            const u32 r[2] = {(u32)(jl < 0 ? 0 : jl > top ? top : jl), (u32)(jr < 0 ? 0 : jr > top ? top : jr)};
+            block_select_ranks<KW, 2>(sm.samp, kept, r, sm.rs2);
+            if (jl >= 0) pl = sm.rs2.result[0];
+            if (jr <= top) pr = sm.rs2.result[1];
+        }
+    }
+    if (threadIdx.x == 0) {
+        g->pl = (u128)pl;
+        g->pr = (u128)pr;
+        g->dst = s.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
+        g->cnt_a = 0;
+        g->cnt_b = 0;
+        g->pending = 1;
+        g->level = s.level + 1;
+        if (grid_level) g->levels_grid++;
+        else g->levels_block++;
+        if (s.level == 0) g->sample_kept = kept;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------- finish in one block
+// At most T undecided elements remain in the source: gather them, select the
+// one of rank k_rem, emit every element not above it.
+
+template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    SelState* g = a.st;
+    const SelState s = *g;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    if (threadIdx.x == 0) sm.kept = 0;
+    __syncthreads();
+    const InputSrc<DT> isrc{static_cast<const raw_t*>(a.keys), s.m_src, a.aligned != 0};
+    const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
+                           a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], s.m_src};
+    for (u64 base = 0; base < s.m_src; base += BLK_NT) {
+        const u64 i = base + threadIdx.x;
+        const bool ok = i < s.m_src;
+        key_t kv = 0;
+        u32 x = 0;
+        if (ok) {
+            if (s.src == SRC_INPUT) isrc.at(i, kv, x);
+            else csrc.at(i, kv, x);
+        }
+        const ct c = C::make(kv, x);
+        const bool keep = ok && c >= lo && c <= hi;
+        const u32 slot = warp_append(keep, &sm.kept);
+        if (keep && slot < Lim<KW>::ELEMS) sm.samp[slot] = c;
+    }
+    __syncthreads();
+    const u32 count = sm.kept;
+    if (count != s.m_win || s.k_rem == 0 || s.k_rem > count || count > Lim<KW>::ELEMS) {
+        if (threadIdx.x == 0) {
+            g->status = ST_EINTERNAL;
+            g->phase = PH_ERROR;
+            latch(a.err, ST_EINTERNAL);
+        }
+        return;
+    }
+    const u32 r[1] = {(u32)(s.k_rem - 1)};
+    block_select_ranks<KW, 1>(sm.samp, count, r, sm.rs1);
+    const ct kth = sm.rs1.result[0];
+    if (threadIdx.x == 0) sm.kept = 0;
+    __syncthreads();
+    raw_t* ok_out = static_cast<raw_t*>(a.out_keys);
+    for (u32 base = 0; base < count; base += BLK_NT) {
+        const u32 i = base + threadIdx.x;
+        const bool in = i < count;
+        const ct c = in ? sm.samp[i] : (ct)0;
+        const bool sel = in && c <= kth;
+        const u32 slot = warp_append(sel, &sm.kept);
+        if (sel) {
+            ok_out[s.out_base + slot] = K::inv((key_t)C::key(c));
+            a.out_idx[s.out_base + slot] = C::idx(c);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        static_cast<raw_t*>(a.kth_key)[0] = K::inv((key_t)C::key(kth));
+        a.kth_idx[0] = C::idx(kth);
+        if (sm.kept != s.k_rem) {
+            g->status = ST_EINTERNAL;
+            g->phase = PH_ERROR;
+            latch(a.err, ST_EINTERNAL);
+        } else {
+            g->out_base = s.out_base + s.k_rem;
+            g->phase = PH_DONE;
+        }
+    }
+}
+
+// ------------------------------------------------------------- kernels
+
+template <int DT> __global__ void __launch_bounds__(BLK_NT) k_plan(SelArgs a, int first) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<BlockSmem<Key<DT>::KW>*>(smem_raw);
+    SelState* g = a.st;
+    if (threadIdx.x == 0) {
+        if (first) init_state<DT>(g, a);
+        else decide(*g);
+        u32 go = g->phase == PH_RUN;
+        if (go && g->m_src <= a.grid_G) {
+            g->phase = PH_FINISH;
+            go = 0;
+        }
+        sm.flag = go;
+    }
+    __syncthreads();
+    if (!sm.flag) return;
+    plan_level<DT>(a, sm, true);
+}
+
+// First level: the source is always the input, so this variant carries no
+// candidate-source code (fewer registers on the pass that reads all n keys).
+template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass_first(SelArgs a) {
+    __shared__ PassSmem<PASS_NT> ps;
+    const SelState s = *a.st;
+    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
+    run_pass<PASS_NT, DT, true>(a, s, blockIdx.x, gridDim.x, ps);
+}
+
+template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass(SelArgs a) {
+    __shared__ PassSmem<PASS_NT> ps;
+    const SelState s = *a.st;
+    if (s.phase != PH_RUN || !s.pending) return;
+    run_pass<PASS_NT, DT>(a, s, blockIdx.x, gridDim.x, ps);
+}
+
+template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, int first) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<BlockSmem<Key<DT>::KW>*>(smem_raw);
+    SelState* g = a.st;
+    if (threadIdx.x == 0) {
+        if (first) init_state<DT>(g, a);
+        else decide(*g);
+        if (g->phase == PH_RUN) g->phase = PH_FINISH;
+        sm.flag = g->phase == PH_FINISH;
+    }
+    __syncthreads();
+    if (!sm.flag) return;
+    for (u32 it = 0; it < MAX_BLOCK_LEVELS; ++it) {
+        if (g->m_src <= a.finish_T) {
+            block_finish<DT>(a, sm);
+            return;
+        }
+        plan_level<DT>(a, sm, false);
+        {
+            const SelState s = *g;
+            run_pass<BLK_NT, DT>(a, s, 0, 1, sm.ps);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) decide(*g);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        g->status = ST_EINTERNAL;
+        g->phase = PH_ERROR;
+        latch(a.err, ST_EINTERNAL);
+    }
+}
+
+// k = 1: the minimum pair (base case of Algorithm "select");
+// k = n: every pair, plus the maximum as the rank-n pair.
+template <int KW> __device__ __forceinline__ typename Comp<KW>::t shfl_xor_ct(typename Comp<KW>::t v, int o);
+template <> __device__ __forceinline__ u64 shfl_xor_ct<32>(u64 v, int o) {
+    return __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+}
+template <> __device__ __forceinline__ u128 shfl_xor_ct<64>(u128 v, int o) {
+    const u64 lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)v, o);
+    const u64 hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)(v >> 64), o);
+    return ((u128)hi << 64) | lo;
+}
+
+template <int KW>
+__device__ typename Comp<KW>::t block_extreme(typename Comp<KW>::t v, bool want_max, typename Comp<KW>::t* red) {
+    typedef typename Comp<KW>::t ct;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ct w = shfl_xor_ct<KW>(v, o);
+        v = want_max ? (w > v ? w : v) : (w < v ? w : v);
+    }
+    const u32 warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane_id() == 0) red[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ct b = red[0];
+        for (u32 w = 1; w < nw; ++w) b = want_max ? (red[w] > b ? red[w] : b) : (red[w] < b ? red[w] : b);
+        red[0] = b;
+    }
+    __syncthreads();
+    const ct out = red[0];
+    __syncthreads();
+    return out;
+}
+
+template <int DT>
+__global__ void __launch_bounds__(EXT_NT) k_extreme(SelArgs a, int want_max, u32* counter, void* partials_v) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    __shared__ ct red[EXT_NT / 32];
+    __shared__ u32 is_last;
+    ct* partials = static_cast<ct*>(partials_v);
+    const InputSrc<DT> src{static_cast<const raw_t*>(a.keys), a.n, a.aligned != 0};
+    const bool copy = want_max != 0; // k = n also copies every pair out
+    raw_t* ok_out = static_cast<raw_t*>(a.out_keys);
+    ct best = want_max ? (ct)0 : C::max_value();
+    constexpr u64 TILE = (u64)EXT_NT * 16;
+    const u64 ntiles = (a.n + TILE - 1) / TILE;
+    for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        typename K::key_t kk[16];
+        u32 ii[16];
+        const u32 valid = src.template load16<EXT_NT>(t * TILE, kk, ii);
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            if (!((valid >> s) & 1u)) continue;
+            const ct c = C::make(kk[s], ii[s]);
+            best = want_max ? (c > best ? c : best) : (c < best ? c : best);
+            if (copy) {
+                ok_out[ii[s]] = K::inv(kk[s]);
+                a.out_idx[ii[s]] = ii[s];
+            }
+        }
+    }
+    best = block_extreme<KW>(best, want_max, red);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = best;
+        __threadfence();
+        const u32 prev = atomicAdd(counter, 1u);
+        is_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    ct v = want_max ? (ct)0 : C::max_value();
+    for (u32 i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        const volatile ct* p = partials;
+        const ct w = p[i];
+        v = want_max ? (w > v ? w : v) : (w < v ? w : v);
+    }
+    v = block_extreme<KW>(v, want_max, red);
+    if (threadIdx.x == 0) {
+        static_cast<raw_t*>(a.kth_key)[0] = K::inv((typename K::key_t)C::key(v));
+        a.kth_idx[0] = C::idx(v);
+        if (!copy) {
+            ok_out[0] = K::inv((typename K::key_t)C::key(v));
+            a.out_idx[0] = C::idx(v);
+        }
+        SelState* g = a.st;
+        init_state<DT>(g, a);
+        g->phase = PH_DONE;
+        g->out_base = a.k;
+        atomicExch(counter, 0u);
+    }
+}
+
+// ----------------------------------------------------------- host side
+
+struct Tuning {
+    u32 sample, parts, T, G;
+    float z;
+    u32 flags;
+    u64 seed;
+};
+
+// Host copy of the device pivot-rank rule, for sizing buffers and predicting
+// the number of grid levels.
+static double est_bracket(u64 m, u64 k_rem, u32 s, float z) {
+    const double kept = (double)std::min<u64>(s, m);
+    const double mu_le = kept * (double)k_rem / (double)m;
+    const double mu_lt = kept * (double)(k_rem - 1) / (double)m;
+    const double v = std::max(0.0, mu_le * (1.0 - mu_le / kept));
+    const double d = z * std::sqrt(v) + z * z / 3.0 + 1.0;
+    const double jl = std::max(-1.0, std::floor(mu_le - d) - 1.0);
+    const double jr = std::min(kept, std::ceil(mu_lt + d));
+    return std::min((double)m, (jr - jl + 1.0) * (double)m / kept);
+}
+
+template <int DT> static topk_status set_smem_attrs() {
+    static bool done = false;
+    if (done) return TOPK_OK;
+    const int bytes = (int)sizeof(BlockSmem<Key<DT>::KW>);
+    if (cudaFuncSetAttribute(k_plan<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return TOPK_ECUDA;
+    if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+        return TOPK_ECUDA;
+    done = true;
+    return TOPK_OK;
+}
+
+// Resident blocks per SM of each pass variant: the grid is one full wave.
+template <int DT> static int pass_grid(topk_ctx* ctx, bool first) {
+    static int occ_first = 0, occ_rest = 0;
+    if (occ_first == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_first, k_pass_first<DT>, PASS_NT, 0) != cudaSuccess)
+            occ_first = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rest, k_pass<DT>, PASS_NT, 0) != cudaSuccess)
+            occ_rest = 1;
+        occ_first = std::max(1, occ_first);
+        occ_rest = std::max(1, occ_rest);
+    }
+    return ctx->sms * (first ? occ_first : occ_rest);
+}
+
+template <int DT>
+static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_keys, u32* out_idx,
+                              void* kth_key, u32* kth_idx, const topk_params* prm, cudaStream_t st) {
+    constexpr int KW = Key<DT>::KW;
+    constexpr u32 ELEMS = Lim<KW>::ELEMS;
+    topk_params p{};
+    if (prm) p = *prm;
+    Tuning tu;
+    tu.sample = p.sample_size ? std::min<u32>(std::max<u32>(p.sample_size, 64), ELEMS) : ELEMS;
+    tu.parts = p.partitions ? p.partitions : (u32)ctx->sms;
+    tu.T = p.finish_threshold ? std::min<u32>(std::max<u32>(p.finish_threshold, 64), ELEMS) : ELEMS;
+    tu.G = 4 * tu.T;
+    tu.z = p.delta_factor > 0.f ? p.delta_factor : 4.0f;
+    tu.flags = p.flags;
+    tu.seed = p.seed ? p.seed : 0x243F6A8885A308D3ull;
+
+    SelArgs a{};
+    a.keys = keys;
+    a.n = n;
+    a.k = k;
+    a.out_keys = out_keys;
+    a.out_idx = out_idx;
+    a.kth_key = kth_key;
+    a.kth_idx = kth_idx;
+    a.st = static_cast<SelState*>(ctx->d_state);
+    a.seed = tu.seed;
+    a.parts = tu.parts;
+    a.sample = tu.sample;
+    a.finish_T = tu.T;
+    a.grid_G = tu.G;
+    a.z = tu.z;
+    a.flags = tu.flags;
+    a.aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    a.err = ctx->d_err;
+    ctx->last_kind = LAST_SELECT;
+
+    if (k == 1 || k == n) {
+        const int grid = ctx->sms * 4;
+        Carve cv;
+        const size_t off_part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)grid);
+        topk_status rs = ensure_scratch(ctx, cv.off);
+        if (rs != TOPK_OK) return rs;
+        char* base = static_cast<char*>(ctx->scratch.base);
+        k_extreme<DT><<<grid, EXT_NT, 0, st>>>(a, k == n && n > 1 ? 1 : 0, ctx->d_counter, base + off_part);
+        return cuda_status(cudaGetLastError());
+    }
+
+    // candidate capacity: room for twice the expected first bracket
+    u64 cap = (u64)(2.0 * est_bracket(n, k, tu.sample, tu.z)) + 4ull * tu.T;
+    if (tu.flags & TOPK_FLAG_TINY_CAND) cap = tu.T;
+    cap = std::max<u64>(cap, tu.T);
+    cap = std::min<u64>(cap, std::max<u64>(n, tu.T));
+    cap = (cap + 4095) & ~(u64)4095;
+    a.cap_b = cap;
+    const size_t kbytes = KW / 8;
+    Carve cv;
+    const size_t off_k0 = cv.take(cap * kbytes), off_k1 = cv.take(cap * kbytes);
+    const size_t off_i0 = cv.take(cap * 4), off_i1 = cv.take(cap * 4);
+    topk_status rs = ensure_scratch(ctx, cv.off);
+    if (rs != TOPK_OK) return rs;
+    char* base = static_cast<char*>(ctx->scratch.base);
+    a.cand_key[0] = base + off_k0;
+    a.cand_key[1] = base + off_k1;
+    a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
+    a.cand_idx[1] = reinterpret_cast<u32*>(base + off_i1);
+
+    if ((rs = set_smem_attrs<DT>()) != TOPK_OK) return rs;
+
+    // grid levels until the candidates fit the block finisher's range
+    int levels = 0;
+    {
+        double m = (double)n, kr = (double)k;
+        while (m > tu.G && levels < 8) {
+            m = 1.5 * est_bracket((u64)m, (u64)std::max(1.0, std::min(kr, m)), tu.sample, tu.z);
+            kr = m / 2;
+            ++levels;
+        }
+    }
+    const size_t smem = sizeof(BlockSmem<KW>);
+    const int grid_first = pass_grid<DT>(ctx, true), grid_rest = pass_grid<DT>(ctx, false);
+    for (int l = 0; l < levels; ++l) {
+        k_plan<DT><<<1, BLK_NT, smem, st>>>(a, l == 0 ? 1 : 0);
+        if (l == 0) k_pass_first<DT><<<grid_first, PASS_NT, 0, st>>>(a);
+        else k_pass<DT><<<grid_rest, PASS_NT, 0, st>>>(a);
+    }
+    k_finish<DT><<<1, BLK_NT, smem, st>>>(a, levels == 0 ? 1 : 0);
+    return cuda_status(cudaGetLastError());
+}
+
+} // namespace topk
+
+using namespace topk;
+
+extern "C" {
+
+topk_status topk_select(topk_ctx* ctx, const void* d_keys, uint64_t n, uint64_t k, topk_dtype dtype,
+                        void* d_out_keys, uint32_t* d_out_idx, void* d_kth_key, uint32_t* d_kth_idx,
+                        const topk_params* params, void* stream) {
+    if (!ctx || !d_keys || !d_out_keys || !d_out_idx || !d_kth_key || !d_kth_idx) return TOPK_EINVAL;
+    const int w = dtype_bytes(dtype);
+    if (w == 0) return TOPK_EINVAL;
+    if (k < 1 || k > n || n > 0xFFFFFFFFull) return TOPK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_keys) % (uintptr_t)w) return TOPK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_out_keys) % (uintptr_t)w) return TOPK_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+    case TOPK_U32: return run_select<DT_U32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    case TOPK_I32: return run_select<DT_I32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    case TOPK_F32: return run_select<DT_F32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    case TOPK_BF16: return run_select<DT_BF16>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    case TOPK_U64: return run_select<DT_U64>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    default: return TOPK_EINVAL;
+    }
+}
+
+topk_status topk_ctx_reserve(topk_ctx* ctx, uint64_t n, topk_dtype dtype) {
+    if (!ctx) return TOPK_EINVAL;
+    const int w = dtype_bytes(dtype);
+    if (w == 0 || n == 0) return TOPK_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
+    const u32 ELEMS = w == 8 ? Lim<64>::ELEMS : Lim<32>::ELEMS;
+    const size_t kbytes = w == 8 ? 8 : 4;
+    // worst first bracket over k (k = n/2), default tuning
+    u64 cap = (u64)(2.0 * est_bracket(n, std::max<u64>(1, n / 2), ELEMS, 4.0f)) + 4ull * ELEMS;
+    cap = std::min<u64>(cap, std::max<u64>(n, ELEMS));
+    cap = (cap + 4095) & ~(u64)4095;
+    Carve cv;
+    cv.take(cap * kbytes);
+    cv.take(cap * kbytes);
+    cv.take(cap * 4);
+    cv.take(cap * 4);
+    return ensure_scratch(ctx, cv.off);
+}
+
+topk_status topk_last_stats(topk_ctx* ctx, topk_stats* out) {
+    if (!ctx || !out) return TOPK_EINVAL;
+    *out = topk_stats{};
+    if (ctx->last_kind != LAST_SELECT) return TOPK_OK;
+    SelState s;
+    if (cudaMemcpy(&s, ctx->d_state, sizeof(SelState), cudaMemcpyDeviceToHost) != cudaSuccess) return TOPK_ECUDA;
+    out->levels_grid = s.levels_grid;
+    out->levels_block = s.levels_block;
+    out->pivot_failures = s.failures;
+    out->overflows = s.overflows;
+    out->first_candidates = s.first_cand;
+    out->sample_kept = s.sample_kept;
+    return TOPK_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,555 @@
+// select_core.cuh — the steps of sample-based selection as block-level device
+// functions, shared by the single-selection kernels (select.cu) and the
+// batched kernel (batched.cu).
+//
+// One recursion level of Algorithm "select" (paper, Section 2) is
+//   pickPivots : draw a sample of the undecided elements, take the sample
+//                elements of ranks k|S|/n -/+ Delta as pivots l <= r
+//                ("Distributed FR-Selection", Section 2);
+//   partition  : split the elements into a (< l), b (l..r), c (> r);
+//   reduction  : n_a, n_b summed over all partitions;
+//   branch     : recurse into a, b or c.
+// Here a pass writes a straight into the output (when the bracket holds rank
+// k they are all selected) and b into a candidate buffer, so one read of the
+// input classifies and compacts.  The reduction is the sum of per-block
+// atomics.  The branch is `decide`, run by one thread before the next level.
+#pragma once
+
+#include "common.cuh"
+
+namespace topk {
+
+// ------------------------------------------------------------------ sources
+// A source yields (key', idx) for positions 0..m-1.
+
+template <int DT> struct InputSrc {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    static constexpr int KW = K::KW;
+    static constexpr int EPV = 16 / (int)sizeof(raw_t); // elements per 16-byte vector
+    static constexpr int NV = 16 / EPV;                 // vectors per 16-element slot set
+    static constexpr bool IMPLICIT_IDX = true; // position = element index
+    const raw_t* keys;
+    u64 m;
+    bool aligned;
+
+    __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
+        k = K::fwd(keys[i]);
+        x = (u32)i;
+    }
+    // position of slot s of this thread in the tile starting at `base`
+    template <int NT> __device__ __forceinline__ static u32 idx_of(u64 base, int s) {
+        return (u32)(base + (u64)((s / EPV) * NT + threadIdx.x) * EPV + (s % EPV));
+    }
+
+    // 16 elements per thread: slot s = j*EPV + i is element
+    // base + (j*NT + tid)*EPV + i.  Bit s of the returned mask = valid.
+    template <int NT>
+    __device__ __forceinline__ u32 load16(u64 base, key_t (&kk)[16], u32 (&ii)[16]) const {
+        const u32 tid = threadIdx.x;
+        if (aligned && base + (u64)NT * 16 <= m) {
+            const uint4* p = reinterpret_cast<const uint4*>(keys) + base / EPV;
+            uint4 v[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) v[j] = ld_stream(p + j * NT + tid);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) {
+                const u64 e0 = base + (u64)(j * NT + tid) * EPV;
+#pragma unroll
+                for (int i = 0; i < EPV; ++i) {
+                    raw_t r;
+                    if (sizeof(raw_t) == 4) {
+                        r = (raw_t)u4get(v[j], i);
+                    } else if (sizeof(raw_t) == 2) {
+                        u32 w = u4get(v[j], i >> 1);
+                        r = (raw_t)((i & 1) ? (w >> 16) : (w & 0xFFFFu));
+                    } else {
+                        r = (raw_t)(((u64)u4get(v[j], 2 * i + 1) << 32) | u4get(v[j], 2 * i));
+                    }
+                    kk[j * EPV + i] = K::fwd(r);
+                    ii[j * EPV + i] = (u32)(e0 + i);
+                }
+            }
+            return 0xFFFFu;
+        }
+        u32 valid = 0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+#pragma unroll
+            for (int i = 0; i < EPV; ++i) {
+                const u64 e = base + (u64)(j * NT + tid) * EPV + i;
+                const int s = j * EPV + i;
+                if (e < m) {
+                    kk[s] = K::fwd(keys[e]);
+                    valid |= 1u << s;
+                } else {
+                    kk[s] = 0;
+                }
+                ii[s] = (u32)e;
+            }
+        }
+        return valid;
+    }
+};
+
+template <int KW> struct CandSrc;
+
+template <> struct CandSrc<32> {
+    typedef u32 key_t;
+    static constexpr int KW = 32;
+    static constexpr bool IMPLICIT_IDX = false;
+    const u32* ck;
+    const u32* ci;
+    u64 m;
+    __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
+        k = __ldcg(ck + i);
+        x = __ldcg(ci + i);
+    }
+    template <int NT>
+    __device__ __forceinline__ u32 load16(u64 base, key_t (&kk)[16], u32 (&ii)[16]) const {
+        const u32 tid = threadIdx.x;
+        if (base + (u64)NT * 16 <= m) {
+            const uint4* pk = reinterpret_cast<const uint4*>(ck) + base / 4;
+            const uint4* pi = reinterpret_cast<const uint4*>(ci) + base / 4;
+            uint4 vk[4], vi[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                vk[j] = __ldcg(pk + j * NT + tid);
+                vi[j] = __ldcg(pi + j * NT + tid);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    kk[j * 4 + i] = u4get(vk[j], i);
+                    ii[j * 4 + i] = u4get(vi[j], i);
+                }
+            return 0xFFFFu;
+        }
+        u32 valid = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const u64 e = base + (u64)(j * NT + tid) * 4 + i;
+                const int s = j * 4 + i;
+                if (e < m) {
+                    kk[s] = __ldcg(ck + e);
+                    ii[s] = __ldcg(ci + e);
+                    valid |= 1u << s;
+                } else {
+                    kk[s] = 0;
+                    ii[s] = 0;
+                }
+            }
+        return valid;
+    }
+};
+
+template <> struct CandSrc<64> {
+    typedef u64 key_t;
+    static constexpr int KW = 64;
+    static constexpr bool IMPLICIT_IDX = false;
+    const u64* ck;
+    const u32* ci;
+    u64 m;
+    __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
+        k = __ldcg(reinterpret_cast<const unsigned long long*>(ck) + i);
+        x = __ldcg(ci + i);
+    }
+    template <int NT>
+    __device__ __forceinline__ u32 load16(u64 base, key_t (&kk)[16], u32 (&ii)[16]) const {
+        const u32 tid = threadIdx.x;
+        if (base + (u64)NT * 16 <= m) {
+            const uint4* pk = reinterpret_cast<const uint4*>(ck) + base / 2;
+            const uint2* pi = reinterpret_cast<const uint2*>(ci) + base / 2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                uint4 vk = __ldcg(pk + j * NT + tid);
+                uint2 vi = __ldcg(pi + j * NT + tid);
+                kk[2 * j] = ((u64)vk.y << 32) | vk.x;
+                kk[2 * j + 1] = ((u64)vk.w << 32) | vk.z;
+                ii[2 * j] = vi.x;
+                ii[2 * j + 1] = vi.y;
+            }
+            return 0xFFFFu;
+        }
+        u32 valid = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const u64 e = base + (u64)(j * NT + tid) * 2 + i;
+                const int s = j * 2 + i;
+                if (e < m) {
+                    at(e, kk[s], ii[s]);
+                    valid |= 1u << s;
+                } else {
+                    kk[s] = 0;
+                    ii[s] = 0;
+                }
+            }
+        return valid;
+    }
+};
+
+// --------------------------------------------------------- output targets
+// Where a pass writes its a elements (selected: raw keys + positions) and its
+// b elements (candidates: key' + positions).
+
+template <int DT> struct Sink {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    raw_t* out_keys;
+    u32* out_idx;
+    u64 out_base; // first free output slot
+    u64 cap_a;    // slots available to this pass (k_rem)
+    key_t* ck;
+    u32* ci;
+    u64 cap_b;
+    u64* cnt_a; // global counters (atomics)
+    u64* cnt_b;
+
+    __device__ __forceinline__ void put_a(u64 pos, key_t k, u32 x) const {
+        if (pos < cap_a) {
+            out_keys[out_base + pos] = K::inv(k);
+            out_idx[out_base + pos] = x;
+        }
+    }
+    __device__ __forceinline__ void put_b(u64 pos, key_t k, u32 x) const {
+        if (pos < cap_b) {
+            ck[pos] = k;
+            ci[pos] = x;
+        }
+    }
+};
+
+// ------------------------------------------------------------ the pass
+// Streams the source in tiles of NT*16 elements, classifies every element
+// against (lo, pl, pr) and compacts a and b.  A tile with neither costs one
+// barrier; otherwise per-warp counts are scanned, one atomic per class and
+// tile reserves output room, and every warp writes its elements slot by slot
+// as contiguous runs (ballot + popc).
+
+template <int NT> struct PassSmem {
+    u32 wa[NT / 32], wb[NT / 32];
+    u64 ba[NT / 32], bb[NT / 32];
+};
+
+template <int NT, bool HAS_A, int DT, class Src>
+__device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
+                           typename Comp<Src::KW>::t lo, typename Comp<Src::KW>::t pl,
+                           typename Comp<Src::KW>::t pr, const Sink<DT>& sink,
+                           PassSmem<NT>& sm) {
+    typedef Comp<Src::KW> C;
+    typedef typename C::t ct;
+    typedef typename Src::key_t key_t;
+    constexpr u64 TILE = (u64)NT * 16;
+    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    const u64 ntiles = (src.m + TILE - 1) / TILE;
+
+    for (u64 t = tile0; t < ntiles; t += tile_step) {
+        key_t kk[16];
+        u32 ii[16];
+        const u32 valid = src.template load16<NT>(t * TILE, kk, ii);
+        const u64 tb = t * TILE;
+        auto pos = [&](int s) -> u32 {
+            if constexpr (Src::IMPLICIT_IDX) return Src::template idx_of<NT>(tb, s);
+            else return ii[s];
+        };
+        u32 ma = 0, mb = 0;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const ct c = C::make(kk[s], pos(s));
+            const bool ge_pl = c >= pl;
+            const bool b = ge_pl && c <= pr;
+            mb |= (u32)b << s;
+            if (HAS_A) {
+                const bool a = !ge_pl && c >= lo;
+                ma |= (u32)a << s;
+            }
+        }
+        ma &= valid;
+        mb &= valid;
+        if (!__syncthreads_or((int)(ma | mb))) continue;
+
+        const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
+        const u32 wb = __reduce_add_sync(0xffffffffu, (u32)__popc(mb));
+        if (lane == 0) {
+            sm.wa[warp] = wa;
+            sm.wb[warp] = wb;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            u64 ta = 0, tb = 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                sm.ba[w] = ta;
+                sm.bb[w] = tb;
+                ta += sm.wa[w];
+                tb += sm.wb[w];
+            }
+            const u64 ga = ta ? atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ta) : 0;
+            const u64 gb = tb ? atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)tb) : 0;
+            for (int w = 0; w < NT / 32; ++w) {
+                sm.ba[w] += ga;
+                sm.bb[w] += gb;
+            }
+        }
+        __syncthreads();
+        u64 ra = sm.ba[warp], rb = sm.bb[warp];
+        const u32 below = lanemask_lt();
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            if (HAS_A) {
+                const u32 bal = __ballot_sync(0xffffffffu, (ma >> s) & 1u);
+                if ((ma >> s) & 1u) sink.put_a(ra + __popc(bal & below), kk[s], pos(s));
+                ra += __popc(bal);
+            }
+            const u32 bal = __ballot_sync(0xffffffffu, (mb >> s) & 1u);
+            if ((mb >> s) & 1u) sink.put_b(rb + __popc(bal & below), kk[s], pos(s));
+            rb += __popc(bal);
+        }
+    }
+}
+
+// ------------------------------------------------------- radix selection
+// Block-wide selection of the elements of given 0-based ranks among
+// v[0..count) (duplicates counted), by most-significant-digit-first radix
+// selection over 8-bit digits of the composite.  Used to read the pivots off
+// the sample (the sample order statistics of ranks k|S|/n -/+ Delta) and the
+// k-th element off the final candidates.  Equivalent to sorting and indexing.
+
+template <int KW, int NTGT> struct RadixSmem {
+    typedef typename Comp<KW>::t ct;
+    u32 hist[NTGT][256];
+    ct prefix[NTGT];
+    ct mask[NTGT];
+    u32 rank[NTGT];
+    u32 done[NTGT];
+    u32 unique[NTGT];
+    ct result[NTGT];
+};
+
+template <int KW, int NTGT>
+__device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, const u32 (&rank)[NTGT],
+                                   RadixSmem<KW, NTGT>& sm) {
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    if (tid < NTGT) {
+        sm.prefix[tid] = 0;
+        sm.mask[tid] = 0;
+        sm.rank[tid] = rank[tid];
+        sm.done[tid] = 0;
+        sm.unique[tid] = 0;
+    }
+    __syncthreads();
+    for (int d = 0; d < C::DIGITS; ++d) {
+        bool all_done = true;
+#pragma unroll
+        for (int t = 0; t < NTGT; ++t) all_done = all_done && sm.done[t];
+        if (all_done) break; // uniform: every thread reads the same smem
+        for (u32 i = tid; i < NTGT * 256; i += blockDim.x) (&sm.hist[0][0])[i] = 0;
+        __syncthreads();
+        ct pfx[NTGT], msk[NTGT];
+        bool live[NTGT];
+#pragma unroll
+        for (int t = 0; t < NTGT; ++t) {
+            pfx[t] = sm.prefix[t];
+            msk[t] = sm.mask[t];
+            live[t] = !sm.done[t];
+        }
+        for (u32 base = 0; base < count; base += blockDim.x) {
+            const u32 i = base + tid;
+            const bool ok = i < count;
+            const ct c = ok ? v[i] : (ct)0;
+            const u32 dig = C::digit(c, d);
+#pragma unroll
+            for (int t = 0; t < NTGT; ++t) {
+                const bool m = ok && live[t] && ((c & msk[t]) == pfx[t]);
+                const u32 grp = __match_any_sync(0xffffffffu, m ? dig : 0x100u);
+                if (m && lane == (u32)(__ffs(grp) - 1)) atomicAdd(&sm.hist[t][dig], (u32)__popc(grp));
+            }
+        }
+        __syncthreads();
+        if (warp < (u32)NTGT && live[warp]) {
+            const int t = warp;
+            u32 h[8], s = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                h[j] = sm.hist[t][lane * 8 + j];
+                s += h[j];
+            }
+            u32 incl = s;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (u32)o) incl += y;
+            }
+            const u32 excl = incl - s;
+            const u32 r = sm.rank[t];
+            if (r >= excl && r < incl) {
+                // the bin of this lane's 8 holding rank r, and the count below it
+                u32 acc = excl, hb = 0;
+                int b = -1;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (b < 0) {
+                        if (r < acc + h[j]) {
+                            b = j;
+                            hb = h[j];
+                        } else {
+                            acc += h[j];
+                        }
+                    }
+                }
+                const u32 bin = lane * 8 + b;
+                const int shift = (C::DIGITS - 1 - d) * 8;
+                sm.prefix[t] = pfx[t] | ((ct)bin << shift);
+                sm.mask[t] = msk[t] | ((ct)0xFFu << shift);
+                sm.rank[t] = r - acc;
+                if (hb == 1) {
+                    sm.unique[t] = 1;
+                    sm.done[t] = 1;
+                } else if (d == C::DIGITS - 1) {
+                    sm.done[t] = 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // Targets fixed on every digit are the prefix itself; a target whose bin
+    // held one element is that element.
+    if (tid < NTGT) sm.result[tid] = sm.prefix[tid];
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < NTGT; ++t) {
+        if (!sm.unique[t]) continue;
+        const ct msk = sm.mask[t], pfx = sm.prefix[t];
+        for (u32 i = tid; i < count; i += blockDim.x)
+            if ((v[i] & msk) == pfx) sm.result[t] = v[i];
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------- sampling
+// Per-partition sampling (Section 2 "Bernoulli sampling"; Section 4.1: the
+// sample is drawn from every PE in proportion to its share).  The source is
+// cut into `parts` equal partitions; draw j belongs to partition
+// j*parts/draws and picks a position uniformly inside it with Philox4x32-10
+// keyed by the seed, counter (j, partition, level, salt).  Draws that fall
+// outside the window are discarded.  Returns the number kept (<= cap).
+
+template <class Src>
+__device__ u32 block_sample(const Src& src, typename Comp<Src::KW>::t lo, typename Comp<Src::KW>::t hi,
+                            u32 draws, u32 parts, u64 seed, u32 level, u32 salt,
+                            typename Comp<Src::KW>::t* samp, u32 cap, u32* kept_smem) {
+    typedef Comp<Src::KW> C;
+    typedef typename C::t ct;
+    const u32 tid = threadIdx.x;
+    if (tid == 0) *kept_smem = 0;
+    __syncthreads();
+    const u64 m = src.m;
+    const u32 p = (u32)((u64)parts < m ? parts : m);
+    constexpr int U = 8;
+    for (u32 base = 0; base < draws; base += blockDim.x * U) {
+        u64 pos[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u32 j = base + u * blockDim.x + tid;
+            ok[u] = j < draws;
+            const u32 part = (u32)((u64)j * p / draws);
+            const u64 plo = (u64)part * m / p, phi = (u64)(part + 1) * m / p;
+            const Philox4 r = philox4x32_10(j, part, level, salt, (u32)seed, (u32)(seed >> 32));
+            pos[u] = plo + (((u64)r.v[0] * (phi - plo)) >> 32);
+        }
+        typename Src::key_t kk[U];
+        u32 ii[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (ok[u]) src.at(pos[u], kk[u], ii[u]);
+            else { kk[u] = 0; ii[u] = 0; }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const ct c = C::make(kk[u], ii[u]);
+            const bool keep = ok[u] && c >= lo && c <= hi;
+            const u32 bal = __ballot_sync(0xffffffffu, keep);
+            u32 slot0 = 0;
+            if (lane_id() == 0 && bal) slot0 = atomicAdd(kept_smem, (u32)__popc(bal));
+            slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+            const u32 slot = slot0 + __popc(bal & lanemask_lt());
+            if (keep && slot < cap) samp[slot] = c;
+        }
+    }
+    __syncthreads();
+    const u32 kept = *kept_smem;
+    __syncthreads();
+    return kept < cap ? kept : cap;
+}
+
+// --------------------------------------------------- branch of "select"
+// Consumes the counters of the pass just run (Algorithm "select": if
+// n_a >= k recurse into a; if n_a + n_b < k recurse into c with
+// k - n_a - n_b; else into b with k - n_a).  a is never materialised apart
+// from the output, so "recurse into a" narrows the window on the same source;
+// "recurse into c" commits a only and narrows the window to [l, hi]; the
+// common case continues on the candidate buffer b.  One thread.
+
+__device__ inline void decide(SelState& s) {
+    if (!s.pending) return;
+    s.pending = 0;
+    const u64 na = s.cnt_a, nb = s.cnt_b;
+    if (s.level == 1) s.first_cand = nb;
+    if (na >= s.k_rem) {          // l too high: answer in a = [lo, pl)
+        s.hi = s.pl - 1;
+        s.m_win = na;
+        s.failures++;
+        return;
+    }
+    s.out_base += na;             // all of a is selected
+    s.k_rem -= na;
+    s.m_win -= na;
+    s.lo = s.pl;
+    if (nb >= s.k_rem) {          // answer in b = [pl, pr]
+        s.hi = s.pr;
+        s.m_win = nb;
+        if (nb <= s.cap_b) {
+            s.src = s.dst;
+            s.m_src = nb;
+        } else {
+            s.overflows++;
+        }
+    } else {
+        s.failures++;             // r too low: window [pl, hi] on same source
+    }
+}
+
+// Pivot ranks in a sample of `kept` elements of a window of m_win elements
+// for rank k_rem: the sample count below the target is binomial with mean
+// kept*k_rem/m_win; the margin is z standard deviations plus z^2/3 + 1, a
+// Bernstein-type allowance that keeps the tails small when the mean is near
+// 0 (the paper's Delta = p^(1/4 + delta) plays this role, Section 2).
+__device__ inline void pivot_ranks(u32 kept, u64 m_win, u64 k_rem, float z, bool raw,
+                                   long long& jl, long long& jr) {
+    const double s = (double)kept;
+    const double mu_le = s * (double)k_rem / (double)m_win;
+    const double mu_lt = s * (double)(k_rem - 1) / (double)m_win;
+    const double zz = (double)z;
+    double dle, dlt;
+    if (raw) {
+        dle = zz;
+        dlt = zz;
+    } else {
+        const double vle = mu_le * (1.0 - mu_le / s), vlt = mu_lt * (1.0 - mu_lt / s);
+        dle = zz * sqrt(vle > 0 ? vle : 0) + zz * zz / 3.0 + 1.0;
+        dlt = zz * sqrt(vlt > 0 ? vlt : 0) + zz * zz / 3.0 + 1.0;
+    }
+    jl = (long long)floor(mu_le - dle) - 1;
+    jr = (long long)ceil(mu_lt + dlt);
+}
+
+} // namespace topk

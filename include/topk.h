@@ -64,6 +64,8 @@ typedef enum {
                                         failures, results stay exact) */
 #define TOPK_FLAG_TINY_CAND 0x4u     /* testing: minimal candidate buffers so
                                         the overflow paths run */
+#define TOPK_FLAG_NO_BULK_COPY 0x8u  /* first pass: per-thread vector loads
+                                        instead of the bulk-copy pipeline */
 
 /* Tuning knobs; a zero field means "choose automatically".  None of them can
  * change a result, only the time taken. */
@@ -173,6 +175,16 @@ topk_status topk_last_stats(topk_ctx *ctx, topk_stats *out);
 
 /* Human-readable name of a status code (static string). */
 const char *topk_status_string(topk_status s);
+
+/* Measurement hooks (off by default).  When enabled, every call on the
+ * context counts its kernel launches, and the first-level pass of
+ * topk_select (the kernel that streams all n keys) is bracketed by CUDA
+ * events recorded on the call's stream.  topk_ctx_profile_read() synchronises
+ * those events and returns the summed pass time in milliseconds, the number
+ * of passes timed and the number of kernel launches since the last reset. */
+topk_status topk_ctx_profile(topk_ctx *ctx, int enable);
+topk_status topk_ctx_profile_read(topk_ctx *ctx, double *pass_ms, uint64_t *passes,
+                                  uint64_t *launches, int reset);
 
 /* Diagnostic: fills d_out[4*i .. 4*i+3] with Philox4x32-10 (Salmon, Moraes,
  * Dror, Shaw, SC'11) of counter {c0 + i, c1, c2, c3} and key {k0, k1}, for

@@ -24,6 +24,7 @@ TOPK_EBUDGET, TOPK_EBUSY, TOPK_EINTERNAL = 5, 6, 7
 TOPK_FLAG_CHECK_SORTED = 0x1
 TOPK_FLAG_RAW_DELTA = 0x2
 TOPK_FLAG_TINY_CAND = 0x4
+TOPK_FLAG_NO_BULK_COPY = 0x8
 
 DTYPE_NAMES = {TOPK_U32: "u32", TOPK_I32: "i32", TOPK_F32: "f32", TOPK_BF16: "bf16",
                TOPK_U64: "u64"}
@@ -81,6 +82,11 @@ def load_library(path: str = LIB_PATH):
     lib.topk_last_stats.restype = st
     lib.topk_status_string.argtypes = [st]
     lib.topk_status_string.restype = ctypes.c_char_p
+    lib.topk_ctx_profile.argtypes = [vp, i32]
+    lib.topk_ctx_profile.restype = st
+    lib.topk_ctx_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64),
+                                          ctypes.POINTER(u64), i32]
+    lib.topk_ctx_profile_read.restype = st
     lib.topk_debug_philox.argtypes = [u32, u32, u32, u32, u32, u32, vp, u32]
     lib.topk_debug_philox.restype = st
     _lib = lib
@@ -156,6 +162,17 @@ class Context:
     def sync(self, stream=None) -> int:
         """topk_status_sync: waits for the stream, returns the latched status."""
         return load_library().topk_status_sync(self.handle, _stream_ptr(stream))
+
+    def profile(self, enable: bool = True):
+        """Count kernel launches and time the first-level pass with CUDA events."""
+        _check(load_library().topk_ctx_profile(self.handle, 1 if enable else 0), "topk_ctx_profile")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        ms, passes, launches = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load_library().topk_ctx_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(passes),
+                                                    ctypes.byref(launches), 1 if reset else 0),
+               "topk_ctx_profile_read")
+        return {"pass_ms": ms.value, "passes": passes.value, "launches": launches.value}
 
     def last_stats(self) -> dict:
         s = topk_stats()

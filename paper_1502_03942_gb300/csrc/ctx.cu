@@ -45,6 +45,35 @@ topk_status ensure_scratch(topk_ctx* ctx, size_t bytes) {
     return TOPK_OK;
 }
 
+static void drain_events(topk_ctx* ctx) {
+    for (int i = 0; i < ctx->ev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(ctx->ev[i][1]) == cudaSuccess &&
+            cudaEventElapsedTime(&ms, ctx->ev[i][0], ctx->ev[i][1]) == cudaSuccess) {
+            ctx->pass_ms += ms;
+            ctx->passes += 1;
+        }
+    }
+    ctx->ev_used = 0;
+}
+
+void profile_pass_begin(topk_ctx* ctx, cudaStream_t st) {
+    if (!ctx->profile) return;
+    if (ctx->ev_used == topk_ctx::MAX_EVENTS) drain_events(ctx);
+    cudaEvent_t* e = ctx->ev[ctx->ev_used];
+    if (!e[0]) {
+        cudaEventCreate(&e[0]);
+        cudaEventCreate(&e[1]);
+    }
+    cudaEventRecord(e[0], st);
+}
+
+void profile_pass_end(topk_ctx* ctx, cudaStream_t st) {
+    if (!ctx->profile) return;
+    cudaEventRecord(ctx->ev[ctx->ev_used][1], st);
+    ctx->ev_used++;
+}
+
 __global__ void k_philox(u32 c0, u32 c1, u32 c2, u32 c3, u32 k0, u32 k1, u32* out, u32 count) {
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
@@ -95,10 +124,35 @@ topk_status topk_ctx_create(topk_ctx** out, int device) {
     return TOPK_OK;
 }
 
+topk_status topk_ctx_profile(topk_ctx* ctx, int enable) {
+    if (!ctx) return TOPK_EINVAL;
+    ctx->profile = enable != 0;
+    return TOPK_OK;
+}
+
+topk_status topk_ctx_profile_read(topk_ctx* ctx, double* pass_ms, uint64_t* passes, uint64_t* launches,
+                                  int reset) {
+    if (!ctx) return TOPK_EINVAL;
+    cudaSetDevice(ctx->device);
+    drain_events(ctx);
+    if (pass_ms) *pass_ms = ctx->pass_ms;
+    if (passes) *passes = ctx->passes;
+    if (launches) *launches = ctx->launches;
+    if (reset) {
+        ctx->pass_ms = 0.0;
+        ctx->passes = 0;
+        ctx->launches = 0;
+    }
+    return TOPK_OK;
+}
+
 void topk_ctx_destroy(topk_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
+    for (int i = 0; i < topk_ctx::MAX_EVENTS; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
     if (ctx->scratch.base) cudaFree(ctx->scratch.base);
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;

@@ -38,6 +38,14 @@ struct topk_ctx {
     void* d_state = nullptr;       // selection state (SelState or RunsState)
     int last_kind = topk::LAST_NONE;
     topk_stats host_stats{};
+    // measurement hooks
+    bool profile = false;
+    uint64_t launches = 0;
+    uint64_t passes = 0;
+    double pass_ms = 0.0;
+    static constexpr int MAX_EVENTS = 256;
+    cudaEvent_t ev[MAX_EVENTS][2] = {};
+    int ev_used = 0;
 };
 
 namespace topk {
@@ -45,6 +53,13 @@ namespace topk {
 // Grows the context scratch to at least `bytes` (synchronising the device
 // when an old block has to be released).
 topk_status ensure_scratch(topk_ctx* ctx, size_t bytes);
+
+// Measurement hooks: count a launch; bracket the first-level pass.
+inline void count_launch(topk_ctx* ctx, uint64_t n = 1) {
+    if (ctx->profile) ctx->launches += n;
+}
+void profile_pass_begin(topk_ctx* ctx, cudaStream_t st);
+void profile_pass_end(topk_ctx* ctx, cudaStream_t st);
 
 // Records a CUDA error; returns TOPK_ECUDA when `e` is not cudaSuccess.
 topk_status cuda_status(cudaError_t e);

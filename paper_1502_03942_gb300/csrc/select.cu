@@ -82,7 +82,7 @@ template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) {
 
 // ------------------------------------------------------------ one pass
 
-template <int NT, int DT, bool INPUT_ONLY = false>
+template <int NT, int DT, bool INPUT_ONLY = false, bool ONLY_EXACT = false>
 __device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 step, PassSmem<NT>& ps) {
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
@@ -101,15 +101,21 @@ __device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 ste
     sink.cnt_a = &a.st->cnt_a;
     sink.cnt_b = &a.st->cnt_b;
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
-    const bool has_a = pl > lo;
+    const bool has_a = pl > lo, exact = ONLY_EXACT || lo != (ct)0;
     if (INPUT_ONLY || s.src == SRC_INPUT) {
         InputSrc<DT> src{static_cast<const raw_t*>(a.keys), s.m_src, a.aligned != 0};
-        if (has_a) pass_tiles<NT, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
-        else pass_tiles<NT, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        if (exact) pass_tiles<NT, true, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else if constexpr (!ONLY_EXACT) {
+            if (has_a) pass_tiles<NT, true, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+            else pass_tiles<NT, false, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        }
     } else if constexpr (!INPUT_ONLY) {
         CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
-        if (has_a) pass_tiles<NT, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
-        else pass_tiles<NT, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        if (exact) pass_tiles<NT, true, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else if constexpr (!ONLY_EXACT) {
+            if (has_a) pass_tiles<NT, true, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+            else pass_tiles<NT, false, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        }
     }
 }
 
@@ -272,6 +278,131 @@ template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass_first(SelArg
     run_pass<PASS_NT, DT, true>(a, s, blockIdx.x, gridDim.x, ps);
 }
 
+// First level, 16-byte-aligned input: a producer warp streams full tiles
+// into a ring of shared-memory stages with bulk (TMA) copies while 8 consumer
+// warps classify and compact, so HBM reads continue through the consumers'
+// barriers.  Every wait is bounded; a timeout latches TOPK_ETIMEOUT and the
+// block winds down without hanging.
+constexpr int TMA_CONS = 256;
+constexpr int TMA_NT = TMA_CONS + 32;
+constexpr u64 WAIT_LIMIT_NS = 200ull * 1000 * 1000;
+
+template <int DT> struct TmaCfg {
+    static constexpr u32 W = sizeof(typename Key<DT>::raw_t);
+    static constexpr u32 TILE = TMA_CONS * 16; // elements per stage
+    static constexpr u32 BYTES = TILE * W;     // 8, 16 or 32 KiB
+    static constexpr u32 STAGES = W == 2 ? 8 : W == 4 ? 6 : 3;
+    static constexpr u32 SMEM = STAGES * BYTES;
+};
+
+template <int DT, bool HAS_A, bool EXACT>
+__device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
+                            uint64_t* empty, u64 my_n, u32* dead, PassSmem<TMA_CONS>& ps) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    typedef Comp<K::KW> C;
+    typedef typename C::t ct;
+    typedef TmaCfg<DT> Cfg;
+    typedef SyncNamed<1, TMA_CONS> Sync;
+    Sink<DT> sink;
+    sink.out_keys = static_cast<raw_t*>(a.out_keys);
+    sink.out_idx = a.out_idx;
+    sink.out_base = s.out_base;
+    sink.cap_a = s.k_rem;
+    sink.ck = static_cast<key_t*>(a.cand_key[s.dst - 1]);
+    sink.ci = a.cand_idx[s.dst - 1];
+    sink.cap_b = a.cap_b;
+    sink.cnt_a = &a.st->cnt_a;
+    sink.cnt_b = &a.st->cnt_b;
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
+    const u32 lane = lane_id();
+    for (u64 i = 0; i < my_n; ++i) {
+        const u32 stg = (u32)(i % Cfg::STAGES);
+        const u32 parity = (u32)((i / Cfg::STAGES) & 1);
+        bool ok = !*(volatile u32*)dead;
+        if (ok && !mbar_wait_bounded(&full[stg], parity, WAIT_LIMIT_NS)) {
+            ok = false;
+            *(volatile u32*)dead = 1;
+            if (lane == 0) latch(a.err, ST_ETIMEOUT);
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        key_t kk[16];
+        if (ok) {
+            InputSrc<DT>::template load16_smem<TMA_CONS>(
+                reinterpret_cast<const uint4*>(stages + (size_t)stg * Cfg::BYTES), kk);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) kk[q] = 0;
+        }
+        __syncwarp();
+        if (ok && lane == 0) mbar_arrive(&empty[stg]); // stage may be refilled
+        const u64 tb = (blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE;
+        auto pos = [&](int q) -> u32 { return InputSrc<DT>::template idx_of<TMA_CONS>(tb, q); };
+        classify_emit<TMA_CONS, HAS_A, EXACT, Sync>(kk, pos, ok ? 0xFFFFu : 0u, lo, pl, pr, sink, ps);
+    }
+    // the ragged last tile, read directly by the block that owns it
+    const u64 nfull = s.m_src / Cfg::TILE;
+    if (s.m_src % Cfg::TILE != 0 && nfull % gridDim.x == blockIdx.x) {
+        InputSrc<DT> src{static_cast<const raw_t*>(a.keys), s.m_src, false};
+        key_t kk[16];
+        u32 ii[16];
+        const u64 tb = nfull * (u64)Cfg::TILE;
+        const u32 valid = src.template load16<TMA_CONS>(tb, kk, ii);
+        auto pos = [&](int q) -> u32 { return InputSrc<DT>::template idx_of<TMA_CONS>(tb, q); };
+        classify_emit<TMA_CONS, HAS_A, EXACT, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
+    }
+}
+
+template <int DT> __global__ void __launch_bounds__(TMA_NT) k_pass_tma(SelArgs a) {
+    typedef TmaCfg<DT> Cfg;
+    typedef typename Key<DT>::raw_t raw_t;
+    extern __shared__ __align__(128) unsigned char stages[];
+    __shared__ __align__(8) uint64_t full[Cfg::STAGES];
+    __shared__ __align__(8) uint64_t empty[Cfg::STAGES];
+    __shared__ PassSmem<TMA_CONS> ps;
+    __shared__ u32 dead;
+    const SelState s = *a.st;
+    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
+    if (threadIdx.x == 0) {
+        for (u32 i = 0; i < Cfg::STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], TMA_CONS / 32);
+        }
+        dead = 0;
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const u64 nfull = s.m_src / Cfg::TILE;
+    const u64 my_n = nfull > blockIdx.x ? (nfull - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    if (threadIdx.x >= TMA_CONS) { // producer warp: one lane issues the copies
+        if (threadIdx.x == TMA_CONS) {
+            const raw_t* keys = static_cast<const raw_t*>(a.keys);
+            for (u64 i = 0; i < my_n; ++i) {
+                const u32 stg = (u32)(i % Cfg::STAGES);
+                if (i >= Cfg::STAGES) {
+                    const u32 parity = (u32)(((i / Cfg::STAGES) - 1) & 1);
+                    if (*(volatile u32*)&dead || !mbar_wait_bounded(&empty[stg], parity, WAIT_LIMIT_NS)) {
+                        *(volatile u32*)&dead = 1;
+                        latch(a.err, ST_ETIMEOUT);
+                        break;
+                    }
+                }
+                const u64 t = blockIdx.x + i * gridDim.x;
+                mbar_arrive_expect_tx(&full[stg], Cfg::BYTES);
+                bulk_g2s(stages + (size_t)stg * Cfg::BYTES, keys + t * Cfg::TILE, Cfg::BYTES, &full[stg]);
+            }
+        }
+        return;
+    }
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename C::t ct;
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl);
+    if (lo != (ct)0) tma_consume<DT, true, true>(a, s, stages, full, empty, my_n, &dead, ps);
+    else if (pl > lo) tma_consume<DT, true, false>(a, s, stages, full, empty, my_n, &dead, ps);
+    else tma_consume<DT, false, false>(a, s, stages, full, empty, my_n, &dead, ps);
+}
+
 template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass(SelArgs a) {
     __shared__ PassSmem<PASS_NT> ps;
     const SelState s = *a.st;
@@ -299,7 +430,7 @@ template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, 
         plan_level<DT>(a, sm, false);
         {
             const SelState s = *g;
-            run_pass<BLK_NT, DT>(a, s, 0, 1, sm.ps);
+            run_pass<BLK_NT, DT, false, true>(a, s, 0, 1, sm.ps);
         }
         __syncthreads();
         if (threadIdx.x == 0) decide(*g);
@@ -434,6 +565,9 @@ static double est_bracket(u64 m, u64 k_rem, u32 s, float z) {
 template <int DT> static topk_status set_smem_attrs() {
     static bool done = false;
     if (done) return TOPK_OK;
+    if (cudaFuncSetAttribute(k_pass_tma<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TmaCfg<DT>::SMEM) != cudaSuccess)
+        return TOPK_ECUDA;
     const int bytes = (int)sizeof(BlockSmem<Key<DT>::KW>);
     if (cudaFuncSetAttribute(k_plan<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return TOPK_ECUDA;
@@ -444,6 +578,17 @@ template <int DT> static topk_status set_smem_attrs() {
 }
 
 // Resident blocks per SM of each pass variant: the grid is one full wave.
+template <int DT> static int tma_grid(topk_ctx* ctx) {
+    static int occ = 0;
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_tma<DT>, TMA_NT, TmaCfg<DT>::SMEM) !=
+                cudaSuccess ||
+            occ < 1)
+            occ = 1;
+    }
+    return ctx->sms * occ;
+}
+
 template <int DT> static int pass_grid(topk_ctx* ctx, bool first) {
     static int occ_first = 0, occ_rest = 0;
     if (occ_first == 0) {
@@ -500,7 +645,10 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
         topk_status rs = ensure_scratch(ctx, cv.off);
         if (rs != TOPK_OK) return rs;
         char* base = static_cast<char*>(ctx->scratch.base);
+        profile_pass_begin(ctx, st);
         k_extreme<DT><<<grid, EXT_NT, 0, st>>>(a, k == n && n > 1 ? 1 : 0, ctx->d_counter, base + off_part);
+        profile_pass_end(ctx, st);
+        count_launch(ctx);
         return cuda_status(cudaGetLastError());
     }
 
@@ -539,10 +687,15 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
     const int grid_first = pass_grid<DT>(ctx, true), grid_rest = pass_grid<DT>(ctx, false);
     for (int l = 0; l < levels; ++l) {
         k_plan<DT><<<1, BLK_NT, smem, st>>>(a, l == 0 ? 1 : 0);
-        if (l == 0) k_pass_first<DT><<<grid_first, PASS_NT, 0, st>>>(a);
+        if (l == 0) profile_pass_begin(ctx, st);
+        if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY))
+            k_pass_tma<DT><<<tma_grid<DT>(ctx), TMA_NT, TmaCfg<DT>::SMEM, st>>>(a);
+        else if (l == 0) k_pass_first<DT><<<grid_first, PASS_NT, 0, st>>>(a);
         else k_pass<DT><<<grid_rest, PASS_NT, 0, st>>>(a);
+        if (l == 0) profile_pass_end(ctx, st);
     }
     k_finish<DT><<<1, BLK_NT, smem, st>>>(a, levels == 0 ? 1 : 0);
+    count_launch(ctx, 2 * (uint64_t)levels + 1);
     return cuda_status(cudaGetLastError());
 }
 

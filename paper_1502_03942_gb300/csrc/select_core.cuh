@@ -43,6 +43,35 @@ template <int DT> struct InputSrc {
         return (u32)(base + (u64)((s / EPV) * NT + threadIdx.x) * EPV + (s % EPV));
     }
 
+    // Keys of the NV 16-byte vectors of one thread, in slot order.
+    __device__ __forceinline__ static void unpack(const uint4 (&v)[NV], key_t (&kk)[16]) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+#pragma unroll
+            for (int i = 0; i < EPV; ++i) {
+                raw_t r;
+                if (sizeof(raw_t) == 4) {
+                    r = (raw_t)u4get(v[j], i);
+                } else if (sizeof(raw_t) == 2) {
+                    u32 w = u4get(v[j], i >> 1);
+                    r = (raw_t)((i & 1) ? (w >> 16) : (w & 0xFFFFu));
+                } else {
+                    r = (raw_t)(((u64)u4get(v[j], 2 * i + 1) << 32) | u4get(v[j], 2 * i));
+                }
+                kk[j * EPV + i] = K::fwd(r);
+            }
+        }
+    }
+
+    // 16 elements per thread from a tile staged in shared memory.
+    template <int NT>
+    __device__ __forceinline__ static void load16_smem(const uint4* stage, key_t (&kk)[16]) {
+        uint4 v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = stage[j * NT + threadIdx.x];
+        unpack(v, kk);
+    }
+
     // 16 elements per thread: slot s = j*EPV + i is element
     // base + (j*NT + tid)*EPV + i.  Bit s of the returned mask = valid.
     template <int NT>
@@ -53,24 +82,9 @@ template <int DT> struct InputSrc {
             uint4 v[NV];
 #pragma unroll
             for (int j = 0; j < NV; ++j) v[j] = ld_stream(p + j * NT + tid);
+            unpack(v, kk);
 #pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                const u64 e0 = base + (u64)(j * NT + tid) * EPV;
-#pragma unroll
-                for (int i = 0; i < EPV; ++i) {
-                    raw_t r;
-                    if (sizeof(raw_t) == 4) {
-                        r = (raw_t)u4get(v[j], i);
-                    } else if (sizeof(raw_t) == 2) {
-                        u32 w = u4get(v[j], i >> 1);
-                        r = (raw_t)((i & 1) ? (w >> 16) : (w & 0xFFFFu));
-                    } else {
-                        r = (raw_t)(((u64)u4get(v[j], 2 * i + 1) << 32) | u4get(v[j], 2 * i));
-                    }
-                    kk[j * EPV + i] = K::fwd(r);
-                    ii[j * EPV + i] = (u32)(e0 + i);
-                }
-            }
+            for (int q = 0; q < 16; ++q) ii[q] = idx_of<NT>(base, q);
             return 0xFFFFu;
         }
         u32 valid = 0;
@@ -238,79 +252,136 @@ template <int NT> struct PassSmem {
     u64 ba[NT / 32], bb[NT / 32];
 };
 
-template <int NT, bool HAS_A, int DT, class Src>
-__device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
-                           typename Comp<Src::KW>::t lo, typename Comp<Src::KW>::t pl,
-                           typename Comp<Src::KW>::t pr, const Sink<DT>& sink,
-                           PassSmem<NT>& sm) {
-    typedef Comp<Src::KW> C;
-    typedef typename C::t ct;
-    typedef typename Src::key_t key_t;
-    constexpr u64 TILE = (u64)NT * 16;
-    const u32 warp = threadIdx.x >> 5, lane = lane_id();
-    const u64 ntiles = (src.m + TILE - 1) / TILE;
+// Barrier among all threads of the block.
+struct SyncBlock {
+    __device__ static int any(int p) { return __syncthreads_or(p); }
+    __device__ static void sync() { __syncthreads(); }
+};
 
-    for (u64 t = tile0; t < ntiles; t += tile_step) {
-        key_t kk[16];
-        u32 ii[16];
-        const u32 valid = src.template load16<NT>(t * TILE, kk, ii);
-        const u64 tb = t * TILE;
-        auto pos = [&](int s) -> u32 {
-            if constexpr (Src::IMPLICIT_IDX) return Src::template idx_of<NT>(tb, s);
-            else return ii[s];
-        };
-        u32 ma = 0, mb = 0;
+// Barrier among the first N threads only (named barrier ID), for kernels with
+// a producer warp that does not take part in the tile processing.
+template <int ID, int N> struct SyncNamed {
+    __device__ static int any(int p) {
+        int r;
+        asm volatile("{\n\t.reg .pred a, b;\n\tsetp.ne.s32 a, %1, 0;\n\t"
+                     "bar.red.or.pred b, %2, %3, a;\n\tselp.s32 %0, 1, 0, b;\n\t}"
+                     : "=r"(r)
+                     : "r"(p), "n"(ID), "n"(N)
+                     : "memory");
+        return r;
+    }
+    __device__ static void sync() { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory"); }
+};
+
+// Classification and compaction of one tile whose 16 elements per thread are
+// in registers; pos(s) gives the position of slot s.
+//
+// Fast path (window starting at the smallest pair, lo = 0): a key below the
+// key of pl is in a; a key inside [key(pl), key(pr)] may be in a, b or c and
+// is classified exactly on the full (key, position) pair; any other key is in
+// c.  So most elements cost one subtraction and one comparison.  EXACT
+// classifies every element on the pair (used when lo > 0, a narrowed window).
+template <int NT, bool HAS_A, bool EXACT, class Sync, int DT, class CT, class KeyT, class PosF>
+__device__ __forceinline__ void classify_emit(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
+                                              const Sink<DT>& sink, PassSmem<NT>& sm) {
+    typedef Comp<Key<DT>::KW> C;
+    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    u32 ma = 0, mb = 0;
+    if (EXACT) {
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            const ct c = C::make(kk[s], pos(s));
+            const CT c = C::make(kk[s], pos(s));
             const bool ge_pl = c >= pl;
-            const bool b = ge_pl && c <= pr;
-            mb |= (u32)b << s;
-            if (HAS_A) {
-                const bool a = !ge_pl && c >= lo;
-                ma |= (u32)a << s;
-            }
+            mb |= (u32)(ge_pl && c <= pr) << s;
+            if (HAS_A) ma |= (u32)(!ge_pl && c >= lo) << s;
         }
         ma &= valid;
         mb &= valid;
-        if (!__syncthreads_or((int)(ma | mb))) continue;
-
-        const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
-        const u32 wb = __reduce_add_sync(0xffffffffu, (u32)__popc(mb));
-        if (lane == 0) {
-            sm.wa[warp] = wa;
-            sm.wb[warp] = wb;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            u64 ta = 0, tb = 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                sm.ba[w] = ta;
-                sm.bb[w] = tb;
-                ta += sm.wa[w];
-                tb += sm.wb[w];
-            }
-            const u64 ga = ta ? atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ta) : 0;
-            const u64 gb = tb ? atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)tb) : 0;
-            for (int w = 0; w < NT / 32; ++w) {
-                sm.ba[w] += ga;
-                sm.bb[w] += gb;
-            }
-        }
-        __syncthreads();
-        u64 ra = sm.ba[warp], rb = sm.bb[warp];
-        const u32 below = lanemask_lt();
+        if (!Sync::any((int)(ma | mb))) return;
+    } else {
+        const KeyT plk = (KeyT)C::key(pl), span = (KeyT)C::key(pr) - plk;
+        u32 hit = 0;
 #pragma unroll
         for (int s = 0; s < 16; ++s) {
-            if (HAS_A) {
-                const u32 bal = __ballot_sync(0xffffffffu, (ma >> s) & 1u);
-                if ((ma >> s) & 1u) sink.put_a(ra + __popc(bal & below), kk[s], pos(s));
-                ra += __popc(bal);
+            hit |= (u32)((KeyT)(kk[s] - plk) <= span) << s;
+            if (HAS_A) ma |= (u32)(kk[s] < plk) << s;
+        }
+        hit &= valid;
+        ma &= valid;
+        if (!Sync::any((int)(ma | hit))) return;
+        if (hit) { // keys equal to a pivot's key: decide on the position
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                if (!((hit >> s) & 1u)) continue;
+                const CT c = C::make(kk[s], pos(s));
+                if (c < pl) ma |= 1u << s;
+                else if (c <= pr) mb |= 1u << s;
             }
+        }
+    }
+
+    const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
+    const u32 wb = __reduce_add_sync(0xffffffffu, (u32)__popc(mb));
+    if (lane == 0) {
+        sm.wa[warp] = wa;
+        sm.wb[warp] = wb;
+    }
+    Sync::sync();
+    if (threadIdx.x == 0) {
+        u64 ta = 0, tb = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            sm.ba[w] = ta;
+            sm.bb[w] = tb;
+            ta += sm.wa[w];
+            tb += sm.wb[w];
+        }
+        const u64 ga = ta ? atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ta) : 0;
+        const u64 gb = tb ? atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)tb) : 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            sm.ba[w] += ga;
+            sm.bb[w] += gb;
+        }
+    }
+    Sync::sync();
+    u64 ra = sm.ba[warp], rb = sm.bb[warp];
+    const u32 below = lanemask_lt();
+    if (HAS_A && __any_sync(0xffffffffu, ma)) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
+            const u32 bal = __ballot_sync(0xffffffffu, (ma >> s) & 1u);
+            if ((ma >> s) & 1u) sink.put_a(ra + __popc(bal & below), kk[s], pos(s));
+            ra += __popc(bal);
+        }
+    }
+    if (__any_sync(0xffffffffu, mb)) {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) {
             const u32 bal = __ballot_sync(0xffffffffu, (mb >> s) & 1u);
             if ((mb >> s) & 1u) sink.put_b(rb + __popc(bal & below), kk[s], pos(s));
             rb += __popc(bal);
         }
+    }
+}
+
+// Register path: every thread loads its 16 elements of each tile itself.
+template <int NT, bool HAS_A, bool EXACT, int DT, class Src>
+__device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
+                           typename Comp<Src::KW>::t lo, typename Comp<Src::KW>::t pl,
+                           typename Comp<Src::KW>::t pr, const Sink<DT>& sink,
+                           PassSmem<NT>& sm) {
+    typedef typename Src::key_t key_t;
+    constexpr u64 TILE = (u64)NT * 16;
+    const u64 ntiles = (src.m + TILE - 1) / TILE;
+    for (u64 t = tile0; t < ntiles; t += tile_step) {
+        key_t kk[16];
+        u32 ii[16];
+        const u64 tb = t * TILE;
+        const u32 valid = src.template load16<NT>(tb, kk, ii);
+        auto pos = [&](int s) -> u32 {
+            if constexpr (Src::IMPLICIT_IDX) return Src::template idx_of<NT>(tb, s);
+            else return ii[s];
+        };
+        classify_emit<NT, HAS_A, EXACT, SyncBlock>(kk, pos, valid, lo, pl, pr, sink, sm);
     }
 }
 
@@ -320,6 +391,13 @@ __device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
 // selection over 8-bit digits of the composite.  Used to read the pivots off
 // the sample (the sample order statistics of ranks k|S|/n -/+ Delta) and the
 // k-th element off the final candidates.  Equivalent to sorting and indexing.
+//
+// Per digit, every element that still matches a target's prefix is counted
+// into that target's 256-bin histogram.  Lanes of a warp holding the same
+// digit are grouped with eight ballots (one per digit bit), so each distinct
+// digit costs one shared-memory atomic per warp even when all keys tie; warps
+// without a matching element skip the grouping.  A target is resolved as
+// soon as its bin holds a single element.
 
 template <int KW, int NTGT> struct RadixSmem {
     typedef typename Comp<KW>::t ct;
@@ -331,6 +409,17 @@ template <int KW, int NTGT> struct RadixSmem {
     u32 unique[NTGT];
     ct result[NTGT];
 };
+
+// Lanes whose 8-bit `dig` equals this lane's (all 32 lanes call).
+__device__ __forceinline__ u32 warp_same_digit(u32 dig) {
+    u32 same = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const u32 bal = __ballot_sync(0xffffffffu, (dig >> b) & 1u);
+        same &= ((dig >> b) & 1u) ? bal : ~bal;
+    }
+    return same;
+}
 
 template <int KW, int NTGT>
 __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, const u32 (&rank)[NTGT],
@@ -366,11 +455,19 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
             const bool ok = i < count;
             const ct c = ok ? v[i] : (ct)0;
             const u32 dig = C::digit(c, d);
+            bool m[NTGT];
+            bool anym = false;
 #pragma unroll
             for (int t = 0; t < NTGT; ++t) {
-                const bool m = ok && live[t] && ((c & msk[t]) == pfx[t]);
-                const u32 grp = __match_any_sync(0xffffffffu, m ? dig : 0x100u);
-                if (m && lane == (u32)(__ffs(grp) - 1)) atomicAdd(&sm.hist[t][dig], (u32)__popc(grp));
+                m[t] = ok && live[t] && ((c & msk[t]) == pfx[t]);
+                anym = anym || m[t];
+            }
+            if (!__any_sync(0xffffffffu, anym)) continue;
+            const u32 same = warp_same_digit(dig);
+#pragma unroll
+            for (int t = 0; t < NTGT; ++t) {
+                const u32 grp = same & __ballot_sync(0xffffffffu, m[t]);
+                if (m[t] && lane == (u32)(__ffs(grp) - 1)) atomicAdd(&sm.hist[t][dig], (u32)__popc(grp));
             }
         }
         __syncthreads();
@@ -437,10 +534,12 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
 // ------------------------------------------------------------- sampling
 // Per-partition sampling (Section 2 "Bernoulli sampling"; Section 4.1: the
 // sample is drawn from every PE in proportion to its share).  The source is
-// cut into `parts` equal partitions; draw j belongs to partition
-// j*parts/draws and picks a position uniformly inside it with Philox4x32-10
-// keyed by the seed, counter (j, partition, level, salt).  Draws that fall
-// outside the window are discarded.  Returns the number kept (<= cap).
+// cut into `parts` equal partitions; draw j belongs to partition j mod parts
+// (so every partition gets the same share of draws, i.e. a share proportional
+// to its size) and picks a position uniformly inside it.  The uniform
+// numbers come from Philox4x32-10 keyed by the seed: the block of counter
+// (j0, level, salt, const) gives draws j0..j0+3.  Draws that fall outside the
+// window are discarded.  Returns the number kept (<= cap).
 
 template <class Src>
 __device__ u32 block_sample(const Src& src, typename Comp<Src::KW>::t lo, typename Comp<Src::KW>::t hi,
@@ -453,18 +552,28 @@ __device__ u32 block_sample(const Src& src, typename Comp<Src::KW>::t lo, typena
     __syncthreads();
     const u64 m = src.m;
     const u32 p = (u32)((u64)parts < m ? parts : m);
-    constexpr int U = 8;
+    // partition q covers [q*len + min(q, rem), ...) with len + (q < rem) elements
+    const u64 len = m / p;
+    const u32 rem = (u32)(m - len * p);
+    constexpr int U = 8; // draws per thread per round: two Philox blocks
     for (u32 base = 0; base < draws; base += blockDim.x * U) {
         u64 pos[U];
         bool ok[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const u32 j = base + u * blockDim.x + tid;
-            ok[u] = j < draws;
-            const u32 part = (u32)((u64)j * p / draws);
-            const u64 plo = (u64)part * m / p, phi = (u64)(part + 1) * m / p;
-            const Philox4 r = philox4x32_10(j, part, level, salt, (u32)seed, (u32)(seed >> 32));
-            pos[u] = plo + (((u64)r.v[0] * (phi - plo)) >> 32);
+        for (int h = 0; h < U / 4; ++h) {
+            // one Philox block gives the four draws j0..j0+3
+            const u32 j0 = base + (h * blockDim.x + tid) * 4;
+            const Philox4 r = philox4x32_10(j0, level, salt, 0x5A3E1Du, (u32)seed, (u32)(seed >> 32));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const u32 j = j0 + q;
+                const int u = h * 4 + q;
+                ok[u] = j < draws;
+                const u32 part = j % p; // draws dealt round-robin: equal share per partition
+                const u64 plo = (u64)part * len + (part < rem ? part : rem);
+                const u64 psz = len + (part < rem ? 1 : 0);
+                pos[u] = plo + (((u64)r.v[q] * psz) >> 32);
+            }
         }
         typename Src::key_t kk[U];
         u32 ii[U];

@@ -166,6 +166,33 @@ topk_status topk_select_batched(topk_ctx *ctx, const void *d_keys,
                                 void *d_kth_keys, uint32_t *d_kth_idx,
                                 const topk_params *params, void *stream);
 
+/* Selection without any allocation: the same computation and result as
+ * topk_select, for callers that cannot allocate device memory at the point
+ * of the call (no counterpart in the paper).  Such callers include code that
+ * runs while a CUDA graph is being captured (cudaMalloc is not permitted
+ * then), code inside another framework's allocator or memory-pool callbacks,
+ * and latency-critical paths that cannot accept the device-wide
+ * synchronisation that cudaMalloc / cudaFree may cause.  The library's
+ * scratch for this call (about 6 MiB: state, counters and candidate buffers)
+ * is a fixed array in device memory that is created when the library is
+ * loaded and held by every GPU that loads it until the process exits.  No
+ * context is needed; the call runs on the current device.
+ *   Arguments as topk_select, with n limited to 2^22 (4194304) keys; larger
+ *   n returns TOPK_EINVAL and enqueues nothing.
+ *   d_status   NULL or one caller-owned uint32 in device memory: set to 0 by
+ *              the call and to a topk_status code if the device work fails.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and sets kernel attributes; make that first call
+ * before any stream capture.  The call itself calls no cudaMalloc, cudaFree
+ * or other allocating routine.  All calls in the process share the one array
+ * per device, which keeps the contents left by the last call: calls whose
+ * work may overlap on the GPU (different streams, or threads) race and must
+ * be serialised by the caller. */
+topk_status topk_select_noalloc(const void *d_keys, uint64_t n, uint64_t k,
+                                topk_dtype dtype, void *d_out_keys, uint32_t *d_out_idx,
+                                void *d_kth_key, uint32_t *d_kth_idx, uint32_t *d_status,
+                                void *stream);
+
 /* Synchronises `stream`, then returns and clears the first error latched by
  * device code of this context (TOPK_OK if none). */
 topk_status topk_status_sync(topk_ctx *ctx, void *stream);

@@ -15,7 +15,9 @@
 // k = 1 (the base case of Algorithm "select", a global minimum) and k = n
 // (everything selected) take one reduction kernel instead.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "select_core.cuh"
@@ -25,6 +27,7 @@ namespace topk {
 constexpr int BLK_NT = 1024;  // planning / finishing block
 constexpr int PASS_NT = 256;  // grid pass block
 constexpr int EXT_NT = 256;   // min / max reduction block
+constexpr int EXT_BLOCKS_PER_SM = 4;
 constexpr u32 MAX_BLOCK_LEVELS = 256;
 
 template <int KW> struct Lim {
@@ -549,6 +552,42 @@ struct Tuning {
     u64 seed;
 };
 
+template <int KW> static Tuning make_tuning(const topk_params* prm, int sms) {
+    constexpr u32 ELEMS = Lim<KW>::ELEMS;
+    topk_params p{};
+    if (prm) p = *prm;
+    Tuning tu;
+    tu.sample = p.sample_size ? std::min<u32>(std::max<u32>(p.sample_size, 64), ELEMS) : ELEMS;
+    tu.parts = p.partitions ? p.partitions : (u32)sms;
+    tu.T = p.finish_threshold ? std::min<u32>(std::max<u32>(p.finish_threshold, 64), ELEMS) : ELEMS;
+    tu.G = 4 * tu.T;
+    tu.z = p.delta_factor > 0.f ? p.delta_factor : 4.0f;
+    tu.flags = p.flags;
+    tu.seed = p.seed ? p.seed : 0x243F6A8885A308D3ull;
+    return tu;
+}
+
+static SelArgs make_args(const void* keys, u64 n, u64 k, void* out_keys, u32* out_idx, void* kth_key,
+                         u32* kth_idx, const Tuning& tu) {
+    SelArgs a{};
+    a.keys = keys;
+    a.n = n;
+    a.k = k;
+    a.out_keys = out_keys;
+    a.out_idx = out_idx;
+    a.kth_key = kth_key;
+    a.kth_idx = kth_idx;
+    a.seed = tu.seed;
+    a.parts = tu.parts;
+    a.sample = tu.sample;
+    a.finish_T = tu.T;
+    a.grid_G = tu.G;
+    a.z = tu.z;
+    a.flags = tu.flags;
+    a.aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    return a;
+}
+
 // Host copy of the device pivot-rank rule, for sizing buffers and predicting
 // the number of grid levels.
 static double est_bracket(u64 m, u64 k_rem, u32 s, float z) {
@@ -562,9 +601,13 @@ static double est_bracket(u64 m, u64 k_rem, u32 s, float z) {
     return std::min((double)m, (jr - jl + 1.0) * (double)m / kept);
 }
 
+// Kernel attributes, set once per device.
 template <int DT> static topk_status set_smem_attrs() {
-    static bool done = false;
-    if (done) return TOPK_OK;
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TOPK_ECUDA;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done_mask.load() & bit) return TOPK_OK;
     if (cudaFuncSetAttribute(k_pass_tma<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TmaCfg<DT>::SMEM) != cudaSuccess)
         return TOPK_ECUDA;
@@ -573,106 +616,64 @@ template <int DT> static topk_status set_smem_attrs() {
         return TOPK_ECUDA;
     if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return TOPK_ECUDA;
-    done = true;
+    done_mask.fetch_or(bit);
     return TOPK_OK;
 }
 
 // Resident blocks per SM of each pass variant: the grid is one full wave.
-template <int DT> static int tma_grid(topk_ctx* ctx) {
+template <int DT> static int tma_grid(int sms) {
     static int occ = 0;
     if (occ == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_tma<DT>, TMA_NT, TmaCfg<DT>::SMEM) !=
-                cudaSuccess ||
-            occ < 1)
-            occ = 1;
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pass_tma<DT>, TMA_NT, TmaCfg<DT>::SMEM) !=
+            cudaSuccess)
+            o = 1;
+        occ = std::max(1, o);
     }
-    return ctx->sms * occ;
+    return sms * occ;
 }
 
-template <int DT> static int pass_grid(topk_ctx* ctx, bool first) {
+template <int DT> static int pass_grid(int sms, bool first) {
     static int occ_first = 0, occ_rest = 0;
     if (occ_first == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_first, k_pass_first<DT>, PASS_NT, 0) != cudaSuccess)
-            occ_first = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_rest, k_pass<DT>, PASS_NT, 0) != cudaSuccess)
-            occ_rest = 1;
-        occ_first = std::max(1, occ_first);
-        occ_rest = std::max(1, occ_rest);
+        int o1 = 0, o2 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_pass_first<DT>, PASS_NT, 0) != cudaSuccess) o1 = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_pass<DT>, PASS_NT, 0) != cudaSuccess) o2 = 1;
+        occ_rest = std::max(1, o2);
+        occ_first = std::max(1, o1);
     }
-    return ctx->sms * (first ? occ_first : occ_rest);
+    return sms * (first ? occ_first : occ_rest);
 }
 
-template <int DT>
-static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_keys, u32* out_idx,
-                              void* kth_key, u32* kth_idx, const topk_params* prm, cudaStream_t st) {
-    constexpr int KW = Key<DT>::KW;
-    constexpr u32 ELEMS = Lim<KW>::ELEMS;
-    topk_params p{};
-    if (prm) p = *prm;
-    Tuning tu;
-    tu.sample = p.sample_size ? std::min<u32>(std::max<u32>(p.sample_size, 64), ELEMS) : ELEMS;
-    tu.parts = p.partitions ? p.partitions : (u32)ctx->sms;
-    tu.T = p.finish_threshold ? std::min<u32>(std::max<u32>(p.finish_threshold, 64), ELEMS) : ELEMS;
-    tu.G = 4 * tu.T;
-    tu.z = p.delta_factor > 0.f ? p.delta_factor : 4.0f;
-    tu.flags = p.flags;
-    tu.seed = p.seed ? p.seed : 0x243F6A8885A308D3ull;
-
-    SelArgs a{};
-    a.keys = keys;
-    a.n = n;
-    a.k = k;
-    a.out_keys = out_keys;
-    a.out_idx = out_idx;
-    a.kth_key = kth_key;
-    a.kth_idx = kth_idx;
-    a.st = static_cast<SelState*>(ctx->d_state);
-    a.seed = tu.seed;
-    a.parts = tu.parts;
-    a.sample = tu.sample;
-    a.finish_T = tu.T;
-    a.grid_G = tu.G;
-    a.z = tu.z;
-    a.flags = tu.flags;
-    a.aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
-    a.err = ctx->d_err;
-    ctx->last_kind = LAST_SELECT;
-
-    if (k == 1 || k == n) {
-        const int grid = ctx->sms * 4;
-        Carve cv;
-        const size_t off_part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)grid);
-        topk_status rs = ensure_scratch(ctx, cv.off);
-        if (rs != TOPK_OK) return rs;
-        char* base = static_cast<char*>(ctx->scratch.base);
-        profile_pass_begin(ctx, st);
-        k_extreme<DT><<<grid, EXT_NT, 0, st>>>(a, k == n && n > 1 ? 1 : 0, ctx->d_counter, base + off_part);
-        profile_pass_end(ctx, st);
-        count_launch(ctx);
-        return cuda_status(cudaGetLastError());
-    }
-
-    // candidate capacity: room for twice the expected first bracket
+// Candidate capacity for a first level over n keys: twice the expected
+// bracket, at least the finisher's range.
+static u64 candidate_capacity(u64 n, u64 k, const Tuning& tu) {
     u64 cap = (u64)(2.0 * est_bracket(n, k, tu.sample, tu.z)) + 4ull * tu.T;
     if (tu.flags & TOPK_FLAG_TINY_CAND) cap = tu.T;
     cap = std::max<u64>(cap, tu.T);
     cap = std::min<u64>(cap, std::max<u64>(n, tu.T));
-    cap = (cap + 4095) & ~(u64)4095;
-    a.cap_b = cap;
-    const size_t kbytes = KW / 8;
-    Carve cv;
-    const size_t off_k0 = cv.take(cap * kbytes), off_k1 = cv.take(cap * kbytes);
-    const size_t off_i0 = cv.take(cap * 4), off_i1 = cv.take(cap * 4);
-    topk_status rs = ensure_scratch(ctx, cv.off);
+    return (cap + 4095) & ~(u64)4095;
+}
+
+// Enqueues one selection whose state, error word and buffers `a` already
+// points to.  k = 1 and k = n need `counter` (zero) and `partials`
+// (EXT grid composites).  `ctx` (may be null) receives the measurement hooks.
+template <int DT>
+static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, int sms, u32* counter,
+                                  void* partials, cudaStream_t st) {
+    constexpr int KW = Key<DT>::KW;
+    const u64 n = a.n, k = a.k;
+    if (k == 1 || k == n) {
+        if (ctx) profile_pass_begin(ctx, st);
+        k_extreme<DT><<<sms * EXT_BLOCKS_PER_SM, EXT_NT, 0, st>>>(a, k == n && n > 1 ? 1 : 0, counter, partials);
+        if (ctx) {
+            profile_pass_end(ctx, st);
+            count_launch(ctx);
+        }
+        return cuda_status(cudaGetLastError());
+    }
+    topk_status rs = set_smem_attrs<DT>();
     if (rs != TOPK_OK) return rs;
-    char* base = static_cast<char*>(ctx->scratch.base);
-    a.cand_key[0] = base + off_k0;
-    a.cand_key[1] = base + off_k1;
-    a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
-    a.cand_idx[1] = reinterpret_cast<u32*>(base + off_i1);
-
-    if ((rs = set_smem_attrs<DT>()) != TOPK_OK) return rs;
-
     // grid levels until the candidates fit the block finisher's range
     int levels = 0;
     {
@@ -684,19 +685,108 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
         }
     }
     const size_t smem = sizeof(BlockSmem<KW>);
-    const int grid_first = pass_grid<DT>(ctx, true), grid_rest = pass_grid<DT>(ctx, false);
     for (int l = 0; l < levels; ++l) {
         k_plan<DT><<<1, BLK_NT, smem, st>>>(a, l == 0 ? 1 : 0);
-        if (l == 0) profile_pass_begin(ctx, st);
+        if (l == 0 && ctx) profile_pass_begin(ctx, st);
         if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY))
-            k_pass_tma<DT><<<tma_grid<DT>(ctx), TMA_NT, TmaCfg<DT>::SMEM, st>>>(a);
-        else if (l == 0) k_pass_first<DT><<<grid_first, PASS_NT, 0, st>>>(a);
-        else k_pass<DT><<<grid_rest, PASS_NT, 0, st>>>(a);
-        if (l == 0) profile_pass_end(ctx, st);
+            k_pass_tma<DT><<<tma_grid<DT>(sms), TMA_NT, TmaCfg<DT>::SMEM, st>>>(a);
+        else if (l == 0) k_pass_first<DT><<<pass_grid<DT>(sms, true), PASS_NT, 0, st>>>(a);
+        else k_pass<DT><<<pass_grid<DT>(sms, false), PASS_NT, 0, st>>>(a);
+        if (l == 0 && ctx) profile_pass_end(ctx, st);
     }
     k_finish<DT><<<1, BLK_NT, smem, st>>>(a, levels == 0 ? 1 : 0);
-    count_launch(ctx, 2 * (uint64_t)levels + 1);
+    if (ctx) count_launch(ctx, 2 * (uint64_t)levels + 1);
     return cuda_status(cudaGetLastError());
+}
+
+template <int DT>
+static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_keys, u32* out_idx,
+                              void* kth_key, u32* kth_idx, const topk_params* prm, cudaStream_t st) {
+    constexpr int KW = Key<DT>::KW;
+    const Tuning tu = make_tuning<KW>(prm, ctx->sms);
+    SelArgs a = make_args(keys, n, k, out_keys, out_idx, kth_key, kth_idx, tu);
+    a.st = static_cast<SelState*>(ctx->d_state);
+    a.err = ctx->d_err;
+    ctx->last_kind = LAST_SELECT;
+
+    const u64 cap = (k == 1 || k == n) ? 0 : candidate_capacity(n, k, tu);
+    a.cap_b = cap;
+    const size_t kbytes = KW / 8;
+    Carve cv;
+    const size_t off_part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)ctx->sms * EXT_BLOCKS_PER_SM);
+    const size_t off_k0 = cv.take(cap * kbytes), off_k1 = cv.take(cap * kbytes);
+    const size_t off_i0 = cv.take(cap * 4), off_i1 = cv.take(cap * 4);
+    topk_status rs = ensure_scratch(ctx, cv.off);
+    if (rs != TOPK_OK) return rs;
+    char* base = static_cast<char*>(ctx->scratch.base);
+    a.cand_key[0] = base + off_k0;
+    a.cand_key[1] = base + off_k1;
+    a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
+    a.cand_idx[1] = reinterpret_cast<u32*>(base + off_i1);
+    return enqueue_select<DT>(ctx, a, tu, ctx->sms, ctx->d_counter, base + off_part, st);
+}
+
+// ------------------------------------------ entry point without allocation
+// topk_select_noalloc runs the same kernels as topk_select, with every piece
+// of scratch (state, error word, block-done counter, reduction partials and
+// the two candidate buffers) in one file-scope device array instead of a
+// context's cudaMalloc'd block.  The array lives in every GPU that loads the
+// library until the process exits.  Host code must not pass the array's name
+// to a kernel (in host code it is only a stand-in for the symbol); its device
+// address is looked up once per device with cudaGetSymbolAddress.
+
+constexpr u64 NOALLOC_MAX_N = 1ull << 22;  // largest n accepted (4 Mi keys)
+constexpr u64 NOALLOC_CAP = 1ull << 18;    // candidate pairs per buffer
+constexpr size_t NA_OFF_STATE = 0;         // SelState
+constexpr size_t NA_OFF_WORDS = 4096;      // [0] error word, [1] block-done counter
+constexpr size_t NA_OFF_PART = 8192;       // per-block composites of the k = 1 / k = n reduction
+constexpr size_t NA_PART_BYTES = 64 * 1024;
+constexpr size_t NA_OFF_CAND = NA_OFF_PART + NA_PART_BYTES;
+constexpr size_t NA_BYTES = NA_OFF_CAND + 2 * NOALLOC_CAP * (8 + 4); // about 6 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[64] = {};
+
+// Device address of the array on the current device `dev` (set-up on first use).
+static topk_status noalloc_base(int dev, char** out) {
+    if (dev < 0 || dev >= 64) return TOPK_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return TOPK_ECUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<char*>(g_noalloc_addr[dev]);
+    return TOPK_OK;
+}
+
+template <int DT>
+static topk_status run_select_noalloc(char* base, int sms, const void* keys, u64 n, u64 k, void* out_keys,
+                                      u32* out_idx, void* kth_key, u32* kth_idx, u32* d_status,
+                                      cudaStream_t st) {
+    constexpr int KW = Key<DT>::KW;
+    static_assert(sizeof(SelState) <= NA_OFF_WORDS, "state region too small");
+    if ((size_t)sms * EXT_BLOCKS_PER_SM * sizeof(typename Comp<KW>::t) > NA_PART_BYTES) return TOPK_EINVAL;
+    const Tuning tu = make_tuning<KW>(nullptr, sms);
+    SelArgs a = make_args(keys, n, k, out_keys, out_idx, kth_key, kth_idx, tu);
+    u32* words = reinterpret_cast<u32*>(base + NA_OFF_WORDS);
+    a.st = reinterpret_cast<SelState*>(base + NA_OFF_STATE);
+    a.err = d_status ? d_status : words;
+    a.cap_b = NOALLOC_CAP;
+    char* cand = base + NA_OFF_CAND;
+    a.cand_key[0] = cand;
+    a.cand_key[1] = cand + NOALLOC_CAP * 8;
+    a.cand_idx[0] = reinterpret_cast<u32*>(cand + 2 * NOALLOC_CAP * 8);
+    a.cand_idx[1] = reinterpret_cast<u32*>(cand + 2 * NOALLOC_CAP * 8 + NOALLOC_CAP * 4);
+    // the error word and the block-done counter must start at zero
+    if (cudaMemsetAsync(words, 0, 2 * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
+    if (d_status && cudaMemsetAsync(d_status, 0, sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
+    return enqueue_select<DT>(nullptr, a, tu, sms, words + 1, base + NA_OFF_PART, st);
 }
 
 } // namespace topk
@@ -722,6 +812,32 @@ topk_status topk_select(topk_ctx* ctx, const void* d_keys, uint64_t n, uint64_t 
     case TOPK_F32: return run_select<DT_F32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
     case TOPK_BF16: return run_select<DT_BF16>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
     case TOPK_U64: return run_select<DT_U64>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+    default: return TOPK_EINVAL;
+    }
+}
+
+topk_status topk_select_noalloc(const void* d_keys, uint64_t n, uint64_t k, topk_dtype dtype,
+                                void* d_out_keys, uint32_t* d_out_idx, void* d_kth_key,
+                                uint32_t* d_kth_idx, uint32_t* d_status, void* stream) {
+    if (!d_keys || !d_out_keys || !d_out_idx || !d_kth_key || !d_kth_idx) return TOPK_EINVAL;
+    const int w = dtype_bytes(dtype);
+    if (w == 0) return TOPK_EINVAL;
+    if (k < 1 || k > n || n > NOALLOC_MAX_N) return TOPK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_keys) % (uintptr_t)w) return TOPK_EINVAL;
+    if (reinterpret_cast<uintptr_t>(d_out_keys) % (uintptr_t)w) return TOPK_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TOPK_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TOPK_ECUDA;
+    char* base = nullptr;
+    topk_status rs = noalloc_base(dev, &base);
+    if (rs != TOPK_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    switch (dtype) {
+    case TOPK_U32: return run_select_noalloc<DT_U32>(base, sms, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, d_status, st);
+    case TOPK_I32: return run_select_noalloc<DT_I32>(base, sms, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, d_status, st);
+    case TOPK_F32: return run_select_noalloc<DT_F32>(base, sms, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, d_status, st);
+    case TOPK_BF16: return run_select_noalloc<DT_BF16>(base, sms, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, d_status, st);
+    case TOPK_U64: return run_select_noalloc<DT_U64>(base, sms, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, d_status, st);
     default: return TOPK_EINVAL;
     }
 }

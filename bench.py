@@ -317,6 +317,24 @@ def run_ours(args):
     return 0
 
 
+def run_probe(spec):
+    """One selection for profilers: DATASET:N:K[:FLAGS] (after one warm-up)."""
+    import torch
+    import paper_1502_03942_gb300 as tk
+    from paper_1502_03942_gb300 import workloads as wl
+    parts = spec.split(":")
+    ds, n, k = parts[0], int(parts[1]), int(parts[2])
+    flags = int(parts[3], 0) if len(parts) > 3 else 0
+    ctx = tk.Context(0)
+    x = wl.device_f32_dataset(ds, n, seed=2)
+    p = tk.make_params(partitions=148, flags=flags)
+    out = tk.topk_select(ctx, x, k, params=p)
+    tk.topk_select(ctx, x, k, params=p, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": spec, "stats": ctx.last_stats()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,11 +342,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", default=None,
+                    help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__
     __graft_entry__.build()
+    if args.probe:
+        return run_probe(args.probe)
     return run_ours(args)
 
 

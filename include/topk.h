@@ -130,11 +130,15 @@ topk_status topk_select(topk_ctx *ctx, const void *d_keys, uint64_t n, uint64_t 
  *   d_run_off  p + 1 uint64 offsets: run r is d_keys[off[r] .. off[r+1]),
  *              non-decreasing within the run; off[0] = 0.
  *   p          number of runs, >= 1.
- *   k          1 <= k <= off[p] < 2^40.
+ *   k          1 <= k <= off[p] < 2^32 (k > off[p] is reported by
+ *              topk_status_sync() as TOPK_EINVAL, the offsets being device
+ *              data); p <= 2^24.
  *   d_split    p uint64: how many of the k smallest lie in run r; the first
  *              d_split[r] keys of run r are selected.
  *   d_kth_key, d_kth_run, d_kth_pos  the pair of rank k: its key, run and
  *              position inside the run.
+ * params->sample_size, when set, is the number of pivots per round
+ * (default 64, at most 256).
  * Ties are ordered by (run, position).  TOPK_FLAG_CHECK_SORTED makes the
  * device verify the runs' order and report TOPK_EINVAL from
  * topk_status_sync() when a run is not sorted. */

@@ -212,6 +212,63 @@ def topk_select(ctx: Context, keys, k: int, params: topk_params | None = None, s
     return out
 
 
+def topk_select_sorted_runs(ctx: Context, keys, run_off, k: int, params: topk_params | None = None,
+                            stream=None, out=None, check: bool = True):
+    """Rank-k selection over p sorted runs of uint64 keys stored back to back.
+
+    ``run_off``: p + 1 uint64 offsets on the device.  Returns (split[p] uint64,
+    kth_key[1] uint64, kth_run[1] uint32, kth_pos[1] uint64)."""
+    torch = _torch()
+    if keys.dtype != torch.uint64 or run_off.dtype != torch.uint64:
+        raise TypeError("keys and run_off must be uint64 tensors")
+    p = run_off.numel() - 1
+    if out is None:
+        out = (torch.empty(max(p, 1), dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device))
+    split, kk, kr, kp = out
+    st = load_library().topk_select_sorted_runs(
+        ctx.handle, _ptr(keys), _ptr(run_off), p, int(k), TOPK_U64, _ptr(split), _ptr(kk), _ptr(kr),
+        _ptr(kp), ctypes.byref(params) if params is not None else None, _stream_ptr(stream))
+    _check(st, "topk_select_sorted_runs")
+    if check:
+        _check(ctx.sync(stream), "topk_select_sorted_runs (device)")
+    return out
+
+
+def topk_select_batched(ctx: Context, keys, row_off, row_k, params: topk_params | None = None,
+                        stream=None, out=None, out_off=None, check: bool = True):
+    """Independent selections over the rows keys[row_off[i]:row_off[i+1]],
+    each with its own k = row_k[i], in one persistent launch.
+
+    ``row_off``: rows + 1 uint64 CUDA offsets; ``row_k``: rows uint32.  The
+    output offsets are the prefix sums of row_k (computed here with torch
+    unless ``out_off`` is given).  Returns (out_keys, out_idx row-local
+    uint32, kth_keys[rows], kth_idx[rows] uint32, out_off)."""
+    torch = _torch()
+    rows = row_k.numel()
+    if out_off is None:
+        out_off = torch.zeros(rows + 1, dtype=torch.int64, device=keys.device)
+        out_off[1:] = torch.cumsum(row_k.view(torch.int32).to(torch.int64), 0)
+        out_off = out_off.view(torch.uint64)
+    total = int(out_off.view(torch.int64)[-1].item())
+    if out is None:
+        out = (torch.empty(max(total, 1), dtype=keys.dtype, device=keys.device),
+               torch.empty(max(total, 1), dtype=torch.uint32, device=keys.device),
+               torch.empty(rows, dtype=keys.dtype, device=keys.device),
+               torch.empty(rows, dtype=torch.uint32, device=keys.device))
+    ok, oi, kk, ki = out
+    st = load_library().topk_select_batched(
+        ctx.handle, _ptr(keys), _ptr(row_off), _ptr(row_k), rows, dtype_code(keys), _ptr(ok), _ptr(oi),
+        _ptr(out_off), _ptr(kk), _ptr(ki), ctypes.byref(params) if params is not None else None,
+        _stream_ptr(stream))
+    _check(st, "topk_select_batched")
+    if check:
+        _check(ctx.sync(stream), "topk_select_batched (device)")
+    return ok, oi, kk, ki, out_off
+
+
 NOALLOC_MAX_N = 1 << 22
 
 

@@ -1,0 +1,266 @@
+// select_block.cuh — one thread block runs whole recursion levels of the
+// selection: planning (sample + pivots), a block-wide pass, the branch, and
+// the final exact selection among at most T candidates.  Used by the
+// single-selection kernels (select.cu: k_plan, k_finish) and by the batched
+// kernel (batched.cu), where every block selects whole rows.
+#pragma once
+
+#include "select_core.cuh"
+
+namespace topk {
+
+constexpr int BLK_NT = 1024;  // planning / finishing block
+constexpr int PASS_NT = 256;  // grid pass block
+constexpr int EXT_NT = 256;   // min / max reduction block
+constexpr int EXT_BLOCKS_PER_SM = 4;
+constexpr u32 MAX_BLOCK_LEVELS = 256;
+
+template <int KW> struct Lim {
+    // sample and finish capacity of one block (128 KiB of composites)
+    static constexpr u32 ELEMS = KW == 32 ? 16384u : 8192u;
+};
+
+template <int KW> struct BlockSmem {
+    typedef typename Comp<KW>::t ct;
+    ct samp[Lim<KW>::ELEMS];
+    RadixSmem<KW, 2> rs2;
+    RadixSmem<KW, 1> rs1;
+    PassSmem<BLK_NT> ps;
+    u32 kept;
+    u32 flag;
+};
+
+__device__ inline void latch(u32* err, u32 code) { atomicCAS(err, 0u, code); }
+
+// All 32 lanes call; returns the slot of this lane's element when `keep`.
+__device__ __forceinline__ u32 warp_append(bool keep, u32* counter) {
+    const u32 bal = __ballot_sync(0xffffffffu, keep);
+    u32 base = 0;
+    if (lane_id() == 0 && bal) base = atomicAdd(counter, (u32)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    return base + __popc(bal & lanemask_lt());
+}
+
+template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) {
+    typedef Comp<Key<DT>::KW> C;
+    g->lo = 0;
+    g->hi = (u128)C::max_value();
+    g->pl = 0;
+    g->pr = 0;
+    g->m_src = a.n;
+    g->m_win = a.n;
+    g->k_rem = a.k;
+    g->out_base = 0;
+    g->cnt_a = 0;
+    g->cnt_b = 0;
+    g->cap_b = a.cap_b;
+    g->first_cand = 0;
+    g->level = 0;
+    g->phase = PH_RUN;
+    g->src = SRC_INPUT;
+    g->dst = SRC_CAND0;
+    g->pending = 0;
+    g->status = ST_OK;
+    g->levels_grid = 0;
+    g->levels_block = 0;
+    g->failures = 0;
+    g->overflows = 0;
+    g->sample_kept = 0;
+}
+
+// ------------------------------------------------------------ one pass
+
+template <int NT, int DT, bool INPUT_ONLY = false, bool ONLY_EXACT = false>
+__device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 step, PassSmem<NT>& ps) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    Sink<DT> sink;
+    sink.out_keys = static_cast<raw_t*>(a.out_keys);
+    sink.out_idx = a.out_idx;
+    sink.out_base = s.out_base;
+    sink.cap_a = s.k_rem;
+    sink.ck = static_cast<key_t*>(a.cand_key[s.dst - 1]);
+    sink.ci = a.cand_idx[s.dst - 1];
+    sink.cap_b = a.cap_b;
+    sink.cnt_a = &a.st->cnt_a;
+    sink.cnt_b = &a.st->cnt_b;
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
+    const bool has_a = pl > lo, exact = ONLY_EXACT || lo != (ct)0;
+    if (INPUT_ONLY || s.src == SRC_INPUT) {
+        const InputSrc<DT> src = InputSrc<DT>::make(a.keys, s.m_src);
+        if (exact) pass_tiles<NT, true, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else if constexpr (!ONLY_EXACT) {
+            if (has_a) pass_tiles<NT, true, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+            else pass_tiles<NT, false, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        }
+    } else if constexpr (!INPUT_ONLY) {
+        CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
+        if (exact) pass_tiles<NT, true, true, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        else if constexpr (!ONLY_EXACT) {
+            if (has_a) pass_tiles<NT, true, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+            else pass_tiles<NT, false, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
+        }
+    }
+}
+
+// ------------------------------------------------------- pickPivots
+// Samples the window, reads the pivots off the sample and arms the next pass.
+
+template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm, bool grid_level) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    SelState* g = a.st;
+    const SelState s = *g;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
+    u32 kept = 0;
+    if (s.m_win > a.finish_T) {
+        u32 draws = grid_level ? a.sample : (u32)min((u64)a.sample, max((u64)1024, s.m_src / 4));
+        if (s.m_win < s.m_src) { // narrowed window: draw more so enough land inside
+            u64 ratio = s.m_src / (s.m_win ? s.m_win : 1);
+            ratio = ratio < 2 ? 2 : ratio > 64 ? 64 : ratio;
+            draws = (u32)min((u64)draws * ratio / 2, (u64)a.sample * 32);
+        }
+        if (s.src == SRC_INPUT) {
+            const InputSrc<DT> src = InputSrc<DT>::make(a.keys, s.m_src);
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+        } else {
+            CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+        }
+        if (kept > 0) {
+            long long jl, jr;
+            pivot_ranks(kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+            const long long top = (long long)kept - 1;
+            const u32 r[2] = {(u32)(jl < 0 ? 0 : jl > top ? top : jl), (u32)(jr < 0 ? 0 : jr > top ? top : jr)};
+            block_select_ranks<KW, 2>(sm.samp, kept, r, sm.rs2);
+            if (jl >= 0) pl = sm.rs2.result[0];
+            if (jr <= top) pr = sm.rs2.result[1];
+        }
+    }
+    if (threadIdx.x == 0) {
+        g->pl = (u128)pl;
+        g->pr = (u128)pr;
+        g->dst = s.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
+        g->cnt_a = 0;
+        g->cnt_b = 0;
+        g->pending = 1;
+        g->level = s.level + 1;
+        if (grid_level) g->levels_grid++;
+        else g->levels_block++;
+        if (s.level == 0) g->sample_kept = kept;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------- finish in one block
+// At most T undecided elements remain in the source: gather them, select the
+// one of rank k_rem, emit every element not above it.
+
+template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    SelState* g = a.st;
+    const SelState s = *g;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    if (threadIdx.x == 0) sm.kept = 0;
+    __syncthreads();
+    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src);
+    const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
+                           a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], s.m_src};
+    for (u64 base = 0; base < s.m_src; base += BLK_NT) {
+        const u64 i = base + threadIdx.x;
+        const bool ok = i < s.m_src;
+        key_t kv = 0;
+        u32 x = 0;
+        if (ok) {
+            if (s.src == SRC_INPUT) isrc.at(i, kv, x);
+            else csrc.at(i, kv, x);
+        }
+        const ct c = C::make(kv, x);
+        const bool keep = ok && c >= lo && c <= hi;
+        const u32 slot = warp_append(keep, &sm.kept);
+        if (keep && slot < Lim<KW>::ELEMS) sm.samp[slot] = c;
+    }
+    __syncthreads();
+    const u32 count = sm.kept;
+    if (count != s.m_win || s.k_rem == 0 || s.k_rem > count || count > Lim<KW>::ELEMS) {
+        if (threadIdx.x == 0) {
+            g->status = ST_EINTERNAL;
+            g->phase = PH_ERROR;
+            latch(a.err, ST_EINTERNAL);
+        }
+        return;
+    }
+    const u32 r[1] = {(u32)(s.k_rem - 1)};
+    block_select_ranks<KW, 1>(sm.samp, count, r, sm.rs1);
+    const ct kth = sm.rs1.result[0];
+    if (threadIdx.x == 0) sm.kept = 0;
+    __syncthreads();
+    raw_t* ok_out = static_cast<raw_t*>(a.out_keys);
+    for (u32 base = 0; base < count; base += BLK_NT) {
+        const u32 i = base + threadIdx.x;
+        const bool in = i < count;
+        const ct c = in ? sm.samp[i] : (ct)0;
+        const bool sel = in && c <= kth;
+        const u32 slot = warp_append(sel, &sm.kept);
+        if (sel) {
+            ok_out[s.out_base + slot] = K::inv((key_t)C::key(c));
+            a.out_idx[s.out_base + slot] = C::idx(c);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        static_cast<raw_t*>(a.kth_key)[0] = K::inv((key_t)C::key(kth));
+        a.kth_idx[0] = C::idx(kth);
+        if (sm.kept != s.k_rem) {
+            g->status = ST_EINTERNAL;
+            g->phase = PH_ERROR;
+            latch(a.err, ST_EINTERNAL);
+        } else {
+            g->out_base = s.out_base + s.k_rem;
+            g->phase = PH_DONE;
+        }
+    }
+}
+
+
+// Recursion levels run by this block alone until at most T elements remain in
+// the source, then the exact finish.  Precondition: no pass pending.
+template <int DT, bool ONLY_EXACT>
+__device__ void block_levels_and_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+    SelState* g = a.st;
+    for (u32 it = 0; it < MAX_BLOCK_LEVELS; ++it) {
+        if (g->m_src <= a.finish_T) {
+            block_finish<DT>(a, sm);
+            return;
+        }
+        plan_level<DT>(a, sm, false);
+        {
+            const SelState s = *g;
+            run_pass<BLK_NT, DT, false, ONLY_EXACT>(a, s, 0, 1, sm.ps);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) decide(*g);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        g->status = ST_EINTERNAL;
+        g->phase = PH_ERROR;
+        latch(a.err, ST_EINTERNAL);
+    }
+}
+
+} // namespace topk

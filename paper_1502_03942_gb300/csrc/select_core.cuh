@@ -29,18 +29,33 @@ template <int DT> struct InputSrc {
     static constexpr int KW = K::KW;
     static constexpr int EPV = 16 / (int)sizeof(raw_t); // elements per 16-byte vector
     static constexpr int NV = 16 / EPV;                 // vectors per 16-element slot set
-    static constexpr bool IMPLICIT_IDX = true; // position = element index
+    static constexpr bool IMPLICIT_IDX = true;          // position = element index
+    // Tiles are laid on the 16-byte-aligned address at or below the first
+    // key: `keys` is that address, `head` the number of keys before the
+    // first one.  Tile coordinates e map to positions e - head; the slots
+    // with e < head or e >= head + m are masked out.  Those extra reads stay
+    // inside 16-byte segments that also hold valid keys.
     const raw_t* keys;
     u64 m;
-    bool aligned;
+    u32 head;
+
+    __host__ __device__ static InputSrc make(const void* p, u64 m) {
+        InputSrc s;
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        s.head = (u32)((a & 15u) / sizeof(raw_t));
+        s.keys = reinterpret_cast<const raw_t*>(a & ~(uintptr_t)15u);
+        s.m = m;
+        return s;
+    }
+    __device__ __forceinline__ u64 extent() const { return m + head; } // in tile coordinates
 
     __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
-        k = K::fwd(keys[i]);
+        k = K::fwd(keys[head + i]);
         x = (u32)i;
     }
     // position of slot s of this thread in the tile starting at `base`
-    template <int NT> __device__ __forceinline__ static u32 idx_of(u64 base, int s) {
-        return (u32)(base + (u64)((s / EPV) * NT + threadIdx.x) * EPV + (s % EPV));
+    template <int NT> __device__ __forceinline__ u32 idx_of(u64 base, int s) const {
+        return (u32)(base + (u64)((s / EPV) * NT + threadIdx.x) * EPV + (s % EPV) - head);
     }
 
     // Keys of the NV 16-byte vectors of one thread, in slot order.
@@ -72,20 +87,27 @@ template <int DT> struct InputSrc {
         unpack(v, kk);
     }
 
-    // 16 elements per thread: slot s = j*EPV + i is element
-    // base + (j*NT + tid)*EPV + i.  Bit s of the returned mask = valid.
+    // 16 elements per thread of the tile at tile coordinate `base`: slot
+    // s = j*EPV + i is tile element base + (j*NT + tid)*EPV + i.  Bit s of the
+    // returned mask = valid; ii receives positions.
     template <int NT>
     __device__ __forceinline__ u32 load16(u64 base, key_t (&kk)[16], u32 (&ii)[16]) const {
         const u32 tid = threadIdx.x;
-        if (aligned && base + (u64)NT * 16 <= m) {
+        const u64 ext = extent();
+        if (base + (u64)NT * 16 <= ext) {
             const uint4* p = reinterpret_cast<const uint4*>(keys) + base / EPV;
             uint4 v[NV];
 #pragma unroll
             for (int j = 0; j < NV; ++j) v[j] = ld_stream(p + j * NT + tid);
             unpack(v, kk);
+            u32 valid = 0xFFFFu;
 #pragma unroll
-            for (int q = 0; q < 16; ++q) ii[q] = idx_of<NT>(base, q);
-            return 0xFFFFu;
+            for (int q = 0; q < 16; ++q) {
+                const u64 e = base + (u64)((q / EPV) * NT + tid) * EPV + (q % EPV);
+                ii[q] = (u32)(e - head);
+                if (e < head) valid &= ~(1u << q);
+            }
+            return valid;
         }
         u32 valid = 0;
 #pragma unroll
@@ -93,14 +115,14 @@ template <int DT> struct InputSrc {
 #pragma unroll
             for (int i = 0; i < EPV; ++i) {
                 const u64 e = base + (u64)(j * NT + tid) * EPV + i;
-                const int s = j * EPV + i;
-                if (e < m) {
-                    kk[s] = K::fwd(keys[e]);
-                    valid |= 1u << s;
+                const int q = j * EPV + i;
+                if (e >= head && e < ext) {
+                    kk[q] = K::fwd(keys[e]);
+                    valid |= 1u << q;
                 } else {
-                    kk[s] = 0;
+                    kk[q] = 0;
                 }
-                ii[s] = (u32)e;
+                ii[q] = (u32)(e - head);
             }
         }
         return valid;
@@ -116,6 +138,7 @@ template <> struct CandSrc<32> {
     const u32* ck;
     const u32* ci;
     u64 m;
+    __device__ __forceinline__ u64 extent() const { return m; }
     __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
         k = __ldcg(ck + i);
         x = __ldcg(ci + i);
@@ -168,6 +191,7 @@ template <> struct CandSrc<64> {
     const u64* ck;
     const u32* ci;
     u64 m;
+    __device__ __forceinline__ u64 extent() const { return m; }
     __device__ __forceinline__ void at(u64 i, key_t& k, u32& x) const {
         k = __ldcg(reinterpret_cast<const unsigned long long*>(ck) + i);
         x = __ldcg(ci + i);
@@ -371,14 +395,14 @@ __device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
                            PassSmem<NT>& sm) {
     typedef typename Src::key_t key_t;
     constexpr u64 TILE = (u64)NT * 16;
-    const u64 ntiles = (src.m + TILE - 1) / TILE;
+    const u64 ntiles = (src.extent() + TILE - 1) / TILE;
     for (u64 t = tile0; t < ntiles; t += tile_step) {
         key_t kk[16];
         u32 ii[16];
         const u64 tb = t * TILE;
         const u32 valid = src.template load16<NT>(tb, kk, ii);
         auto pos = [&](int s) -> u32 {
-            if constexpr (Src::IMPLICIT_IDX) return Src::template idx_of<NT>(tb, s);
+            if constexpr (Src::IMPLICIT_IDX) return src.template idx_of<NT>(tb, s);
             else return ii[s];
         };
         classify_emit<NT, HAS_A, EXACT, SyncBlock>(kk, pos, valid, lo, pl, pr, sink, sm);

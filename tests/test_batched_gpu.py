@@ -1,0 +1,128 @@
+"""topk_select_batched on the GPU against the CPU oracle (bit-exact per row).
+
+Rows of uneven length at arbitrary (unaligned) offsets, each with its own k,
+in one persistent launch; every key type; the full batched configuration
+(4096 rows, lengths 2^U(10,18), N(0,3) keys, k in 1..1024) checked against the
+oracle on a sample of rows and by properties on all rows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_03942_gb300 import workloads as wl
+
+from _gpu import bits_of, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03942_gb300 as tk
+    return tk
+
+
+@pytest.fixture(scope="module")
+def ctx(tk):
+    c = tk.Context(0)
+    yield c
+    c.close()
+
+
+def rows_for(name, rows, lo, hi, kmax, seed):
+    g = np.random.Generator(np.random.Philox(seed))
+    lens = np.floor(2.0 ** g.uniform(lo, hi, size=rows)).astype(np.uint64)
+    off = np.zeros(rows + 1, np.uint64)
+    off[1:] = np.cumsum(lens)
+    total = int(off[-1])
+    ks = np.minimum(g.integers(1, kmax + 1, size=rows).astype(np.uint64), lens).astype(np.uint32)
+    if name in ("u32", "i32"):
+        keys = wl.uniform_u32(total, seed)
+    elif name == "f32":
+        keys = wl.normal_f32(total, seed, 3.0).view(np.uint32)
+    elif name == "bf16":
+        keys = g.integers(0, 1 << 16, size=total).astype(np.uint16)
+    else:
+        keys = (g.integers(0, 50, size=total).astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15))
+    return keys, off, ks
+
+
+def run(tk, ctx, keys, off, ks, name):
+    d_keys = to_device(keys, name)
+    d_off = to_device(off, "u64")
+    d_k = to_device(ks, "u32")
+    return tk.topk_select_batched(ctx, d_keys, d_off, d_k)
+
+
+def check_rows(keys, off, ks, name, res, rows_to_check):
+    ok, oi, kk, ki, out_off = res
+    got_idx, got_keys = bits_of(oi), bits_of(ok)
+    got_kth_idx, got_kth_key = bits_of(ki), bits_of(kk)
+    oo = bits_of(out_off).astype(np.int64)
+    for i in rows_to_check:
+        row = keys[int(off[i]):int(off[i + 1])]
+        want_sel, want_kth = oracle.select(row, name, int(ks[i]))
+        a, b = oo[i], oo[i + 1]
+        assert np.array_equal(np.sort(got_idx[a:b]), np.sort(want_sel)), f"row {i} set differs"
+        assert np.array_equal(got_keys[a:b], row[got_idx[a:b]]), f"row {i} keys"
+        assert got_kth_idx[i] == want_kth and got_kth_key[i] == row[want_kth], f"row {i} kth"
+
+
+@pytest.mark.parametrize("name", ["u32", "i32", "f32", "bf16", "u64"])
+def test_batched_small(tk, ctx, name):
+    keys, off, ks = rows_for(name, 300, 0, 15, 1024, seed=41)
+    res = run(tk, ctx, keys, off, ks, name)
+    check_rows(keys, off, ks, name, res, range(300))
+
+
+def test_batched_k_extremes(tk, ctx):
+    """k = 1 and k = n in rows longer and shorter than one block's capacity."""
+    g = np.random.Generator(np.random.Philox(43))
+    lens = np.array([1, 2, 5000, 40000, 70000, 16384, 16385, 3], np.uint64)
+    off = np.zeros(lens.size + 1, np.uint64)
+    off[1:] = np.cumsum(lens)
+    keys = g.integers(0, 100, size=int(off[-1])).astype(np.uint32)
+    for ks in (np.ones(lens.size, np.uint32), lens.astype(np.uint32)):
+        res = run(tk, ctx, keys, off, ks, "u32")
+        check_rows(keys, off, ks, "u32", res, range(lens.size))
+
+
+def test_batched_rejects_bad_k(tk, ctx):
+    keys, off, ks = rows_for("u32", 10, 3, 8, 10, seed=44)
+    ks[3] = 0
+    with pytest.raises(tk.TopkError) as e:
+        run(tk, ctx, keys, off, ks, "u32")
+    assert e.value.status == tk.TOPK_EINVAL
+
+
+def test_batched_config_full_size(tk, ctx):
+    """4096 rows, lengths 2^U(10,18), N(0,3) f32, k in 1..1024."""
+    keys, off, ks = wl.batched_rows(4096, 10, 18, 1024, seed=4)
+    bits = keys.view(np.uint32)
+    res = run(tk, ctx, bits, off, ks, "f32")
+    g = np.random.Generator(np.random.Philox(45))
+    sample = sorted(set(g.integers(0, 4096, size=150).tolist()) | {0, 4095})
+    check_rows(bits, off, ks, "f32", res, sample)
+    # every row: k outputs, all distinct, each <= the rank-k pair, and exactly
+    # k - 1 pairs of the row below the rank-k pair (keys have no NaN / -0)
+    ok, oi, kk, ki, out_off = res
+    idx = bits_of(oi).astype(np.int64)
+    oo = bits_of(out_off).astype(np.int64)
+    kth_idx = bits_of(ki).astype(np.int64)
+    kth_key = keys[off[:-1].astype(np.int64) + kth_idx]
+    row_of_el = np.repeat(np.arange(4096), np.diff(off).astype(np.int64))
+    pos_in_row = np.arange(int(off[-1])) - off[:-1].astype(np.int64)[row_of_el]
+    kv = kth_key[row_of_el]
+    below = (keys < kv) | ((keys == kv) & (pos_in_row < kth_idx[row_of_el]))
+    counts = np.bincount(row_of_el, weights=below, minlength=4096).astype(np.int64)
+    assert np.array_equal(counts, ks.astype(np.int64) - 1)
+    assert np.array_equal(np.diff(oo), ks.astype(np.int64))
+    row_of_out = np.repeat(np.arange(4096), ks.astype(np.int64))
+    sel_keys = keys[off[:-1].astype(np.int64)[row_of_out] + idx]
+    kvo = kth_key[row_of_out]
+    assert np.all((sel_keys < kvo) | ((sel_keys == kvo) & (idx <= kth_idx[row_of_out])))
+    # distinct positions per row
+    combo = row_of_out.astype(np.int64) * (1 << 32) + idx
+    assert np.unique(combo).size == combo.size

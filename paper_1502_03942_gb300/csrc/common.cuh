@@ -164,7 +164,8 @@ struct alignas(16) SelState {
     u32 pending;          // a pass ran whose counters are not yet consumed
     u32 status;           // first device error, ST_*
     u32 levels_grid, levels_block, failures, overflows;
-    u32 sample_kept, pad0;
+    u32 sample_kept;
+    u32 dense;            // the armed pass expects many a-elements
 };
 
 // Arguments common to every kernel of one topk_select call.
@@ -188,7 +189,32 @@ struct SelArgs {
     u32 flags;
     u32 aligned;              // input is 16-byte aligned
     u32* err;                 // context's latched error word
+    // grid-level sampling (k_sample / k_pivots) and the end-of-pass branch
+    void* samp;               // sample composites, capacity samp_cap
+    u32* samp_count;          // number drawn into samp (zero between levels)
+    u32* hist;                // HIST_BINS bins over the window (zero between levels)
+    u32* pass_done;           // block-done counter of the pass (zero between passes)
+    u32 samp_cap;
 };
+
+// Histogram of a window [lo, hi]: bin = (c - lo) >> sh with the shift chosen
+// so that every composite of the window falls in one of HIST_BINS bins.
+constexpr u32 HIST_BITS = 12;
+constexpr u32 HIST_BINS = 1u << HIST_BITS;
+
+__device__ __forceinline__ int bit_length_fast(u64 v) { return v ? 64 - __clzll((long long)v) : 0; }
+__device__ __forceinline__ int bit_length_fast(u128 v) {
+    const u64 hi = (u64)(v >> 64);
+    return hi ? 128 - __clzll((long long)hi) : bit_length_fast((u64)v);
+}
+template <class CT> __device__ __forceinline__ u32 hist_shift(CT lo, CT hi) {
+    const int b = bit_length_fast((CT)(hi - lo));
+    return b > (int)HIST_BITS ? (u32)(b - HIST_BITS) : 0u;
+}
+template <class CT> __device__ __forceinline__ u32 hist_bin(CT c, CT lo, u32 sh) {
+    const CT d = (CT)(c - lo) >> sh;
+    return d < (CT)HIST_BINS ? (u32)d : HIST_BINS - 1;
+}
 
 // ---------------------------------------------------------- warp helpers
 

@@ -2,16 +2,17 @@
 // (paper, Section 2, Algorithm "select"; Section 4.1, Theorem "selectFR").
 //
 // Launch sequence of one call (all on the caller's stream, no host round
-// trip):
-//   k_plan   (1 block)  level 1: initialise the state, sample, pivots
-//   k_pass   (grid)     level 1: stream the input once, a -> output,
-//                       b -> candidate buffer 0, block sums -> n_a, n_b
-//   k_plan / k_pass     levels 2..L on the candidate buffers (L predicted on
-//                       the host; a level whose state is already small
-//                       returns at once)
-//   k_finish (1 block)  remaining levels inside one block until at most T
-//                       candidates are left, then selects rank k among them,
-//                       writes the rest of the output and the rank-k pair.
+// trip), per recursion level:
+//   k_sample (grid)     per-partition draws of the current window -> sample
+//                       array + histogram over the window
+//   k_pivots (1 block)  pivots = sample elements of ranks k|S|/n -/+ Delta,
+//                       read off the histogram and refined in two bins
+//   k_pass   (grid)     one read of the source: a -> output, b -> candidate
+//                       buffer; the last block takes the branch
+// then k_finish (1 block): remaining levels inside one block until at most T
+// candidates are left, selection of rank k among them, the rest of the output
+// and the rank-k pair.  The host predicts the number of grid levels; a level
+// whose state is already small returns at once.
 // k = 1 (the base case of Algorithm "select", a global minimum) and k = n
 // (everything selected) take one reduction kernel instead.
 #include <algorithm>
@@ -26,61 +27,317 @@ namespace topk {
 
 // ------------------------------------------------------------- kernels
 
-template <int DT> __global__ void __launch_bounds__(BLK_NT) k_plan(SelArgs a, int first) {
+// Read-after-atomics: the pass counters as the last block of the pass sees them.
+__device__ __forceinline__ u64 atomic_read(u64* p) {
+    return atomicAdd(reinterpret_cast<unsigned long long*>(p), 0ull);
+}
+
+// The branch of Algorithm "select", taken by the last block of a pass once
+// every block's counts are in (block-done counter; nobody waits).  The calling
+// thread must be the block's thread 0, after the block's own atomics.
+__device__ __forceinline__ void pass_epilogue(const SelArgs& a) {
+    __threadfence();
+    const u32 prev = atomicAdd(a.pass_done, 1u);
+    if (prev == gridDim.x - 1) {
+        __threadfence();
+        SelState* g = a.st;
+        g->cnt_a = atomic_read(&g->cnt_a);
+        g->cnt_b = atomic_read(&g->cnt_b);
+        decide(*g);
+        *a.pass_done = 0;
+    }
+}
+
+// ---- pickPivots, part 1: the sample (whole grid)
+// Every thread makes SMP_DRAWS per-partition draws of the current window,
+// appends the kept ones to the sample array and counts them in a shared
+// histogram over the window, added to the global histogram at the end.
+constexpr int SMP_NT = 128;
+constexpr int SMP_DRAWS = 4;        // one Philox block per thread
+constexpr u32 SMP_MAX_SCALE = 4;    // extra draws for a narrowed window
+
+template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, int first) {
+    typedef Key<DT> K;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    __shared__ u32 hist[HIST_BINS];
+    for (u32 i = threadIdx.x; i < HIST_BINS; i += blockDim.x) hist[i] = 0;
+    SelState s;
+    if (first) {
+        s.lo = 0;
+        s.hi = (u128)C::max_value();
+        s.m_src = a.n;
+        s.m_win = a.n;
+        s.src = SRC_INPUT;
+        s.level = 0;
+        s.phase = PH_RUN;
+    } else {
+        s = *a.st;
+    }
+    __syncthreads();
+    if (s.phase != PH_RUN || s.m_src <= a.grid_G || s.m_win <= a.finish_T) return;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    const u32 sh = hist_shift(lo, hi);
+    u32 draws = a.sample;
+    if (s.m_win < s.m_src) { // narrowed window: draw more so that enough land inside
+        u64 ratio = s.m_src / (s.m_win ? s.m_win : 1);
+        ratio = ratio < 1 ? 1 : ratio > SMP_MAX_SCALE ? SMP_MAX_SCALE : ratio;
+        draws = (u32)((u64)draws * ratio);
+    }
+    const u64 m = s.m_src;
+    const u32 p = (u32)((u64)a.parts < m ? a.parts : m);
+    const u64 len = m / p;
+    const u32 rem = (u32)(m - len * p);
+    const u32 j0 = (blockIdx.x * SMP_NT + threadIdx.x) * SMP_DRAWS;
+    const Philox4 r = philox4x32_10(j0, s.level, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
+    key_t kk[SMP_DRAWS];
+    u32 ii[SMP_DRAWS];
+    bool ok[SMP_DRAWS];
+    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, m);
+    const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
+                           a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], m};
+#pragma unroll
+    for (int q = 0; q < SMP_DRAWS; ++q) {
+        const u32 j = j0 + q;
+        ok[q] = j < draws;
+        const u32 part = j % p; // draws dealt round-robin: an equal share per partition
+        const u64 plo = (u64)part * len + (part < rem ? part : rem);
+        const u64 psz = len + (part < rem ? 1 : 0);
+        const u64 pos = plo + (((u64)r.v[q] * psz) >> 32);
+        kk[q] = 0;
+        ii[q] = 0;
+        if (ok[q]) {
+            if (s.src == SRC_INPUT) isrc.at(pos, kk[q], ii[q]);
+            else csrc.at(pos, kk[q], ii[q]);
+        }
+    }
+    ct* samp = static_cast<ct*>(a.samp);
+#pragma unroll
+    for (int q = 0; q < SMP_DRAWS; ++q) {
+        const ct c = C::make(kk[q], ii[q]);
+        const bool keep = ok[q] && c >= lo && c <= hi;
+        const u32 bal = __ballot_sync(0xffffffffu, keep);
+        u32 slot0 = 0;
+        if (lane_id() == 0 && bal) slot0 = atomicAdd(a.samp_count, (u32)__popc(bal));
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        const u32 slot = slot0 + __popc(bal & lanemask_lt());
+        if (keep && slot < a.samp_cap) {
+            samp[slot] = c;
+            atomicAdd(&hist[hist_bin(c, lo, sh)], 1u);
+        } else {
+            ok[q] = false;
+        }
+    }
+    __syncthreads();
+    // each touched bin is moved to the global histogram once (the first
+    // thread to take it)
+#pragma unroll
+    for (int q = 0; q < SMP_DRAWS; ++q) {
+        if (!ok[q]) continue;
+        const u32 b = hist_bin(C::make(kk[q], ii[q]), lo, sh);
+        const u32 v = atomicExch(&hist[b], 0u);
+        if (v) atomicAdd(a.hist + b, v);
+    }
+}
+
+// ---- pickPivots, part 2 (one block): pivots from the histogram and the
+// sample.  The bins holding sample ranks k|S|/n -/+ Delta are found from the
+// histogram's prefix sums; only the sample elements of those bins are
+// gathered and ranked exactly.  Leaves the histogram and the sample count at
+// zero for the next level.
+constexpr int PIV_NT = 1024;
+
+template <int KW> struct PivotSmem {
+    typedef typename Comp<KW>::t ct;
+    ct buf[Lim<KW>::ELEMS];
+    u32 warp_sum[PIV_NT / 32];
+    RadixSmem<KW, 2> rs2;
+    RadixSmem<KW, 1> rs1;
+    u32 bin[2], base[2], cnt[2], want[2];
+    u32 flag, collect, kept;
+    long long jl, jr;
+    u32 whist[2][256];
+    ct wres[2];
+};
+
+constexpr u32 WARP_SELECT_MAX = 4096; // bins up to this size are ranked by one warp
+
+template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, int first) {
+    constexpr int KW = Key<DT>::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<BlockSmem<Key<DT>::KW>*>(smem_raw);
+    auto& sm = *reinterpret_cast<PivotSmem<KW>*>(smem_raw);
     SelState* g = a.st;
-    if (threadIdx.x == 0) {
+    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    if (tid == 0) {
         if (first) init_state<DT>(g, a);
-        else decide(*g);
         u32 go = g->phase == PH_RUN;
         if (go && g->m_src <= a.grid_G) {
             g->phase = PH_FINISH;
             go = 0;
         }
         sm.flag = go;
+        sm.collect = g->m_win <= a.finish_T;
+        const u32 c = *a.samp_count;
+        sm.kept = c < a.samp_cap ? c : a.samp_cap;
+        // pivot ranks once (FP64 is slow on this part; the block shares them)
+        long long jl = -1, jr = 0;
+        if (go && sm.kept > 0)
+            pivot_ranks(sm.kept, g->m_win, g->k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+        sm.jl = jl;
+        sm.jr = jr;
+        for (int q = 0; q < 2; ++q) {
+            sm.bin[q] = 0xFFFFFFFFu;
+            sm.base[q] = 0;
+            sm.cnt[q] = 0;
+        }
     }
     __syncthreads();
-    if (!sm.flag) return;
-    plan_level<DT>(a, sm, true);
+    if (sm.flag) {
+        const SelState s = *g;
+        const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+        ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
+        const u32 kept = sm.kept;
+        const long long jl = sm.jl, jr = sm.jr;
+        if (!sm.collect && kept > 0) {
+            const long long top = (long long)kept - 1;
+            const u32 rl = (u32)(jl < 0 ? 0 : jl > top ? top : jl);
+            const u32 rr = (u32)(jr < 0 ? 0 : jr > top ? top : jr);
+            // exclusive prefix of the histogram (4 bins per thread)
+            u32 h[4], t = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                h[q] = a.hist[tid * 4 + q];
+                t += h[q];
+            }
+            u32 incl = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (u32)o) incl += y;
+            }
+            if (lane == 31) sm.warp_sum[warp] = incl;
+            __syncthreads();
+            if (tid == 0) {
+                u32 acc = 0;
+                for (int w = 0; w < PIV_NT / 32; ++w) {
+                    const u32 v = sm.warp_sum[w];
+                    sm.warp_sum[w] = acc;
+                    acc += v;
+                }
+            }
+            __syncthreads();
+            u32 run = sm.warp_sum[warp] + incl - t;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const u32 b = tid * 4 + q;
+                // bin holding sample rank rl / rr
+                if (h[q] && rl >= run && rl < run + h[q]) {
+                    sm.bin[0] = b;
+                    sm.base[0] = run;
+                    sm.cnt[0] = h[q];
+                }
+                if (h[q] && rr >= run && rr < run + h[q]) {
+                    sm.bin[1] = b;
+                    sm.base[1] = run;
+                    sm.cnt[1] = h[q];
+                }
+                run += h[q];
+            }
+            if (tid == 0) {
+                sm.want[0] = 0;
+                sm.want[1] = 0;
+            }
+            __syncthreads();
+            // gather the two bins (one region if they coincide)
+            const u32 sh = hist_shift(lo, hi);
+            const u32 b0 = sm.bin[0], b1 = sm.bin[1];
+            const bool same = b0 == b1;
+            const u32 off1 = same ? 0 : sm.cnt[0];
+            const ct* samp = static_cast<const ct*>(a.samp);
+            constexpr int U = 8; // loads in flight per thread
+            for (u32 base = 0; base < kept; base += PIV_NT * U) {
+                ct cv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const u32 i = base + u * PIV_NT + tid;
+                    cv[u] = i < kept ? samp[i] : (ct)0;
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const u32 i = base + u * PIV_NT + tid;
+                    const u32 b = i < kept ? hist_bin(cv[u], lo, sh) : 0xFFFFFFFFu;
+                    const bool in0 = b == b0, in1 = !same && b == b1;
+                    const u32 s0 = warp_append(in0, &sm.want[0]);
+                    const u32 s1 = warp_append(in1, &sm.want[1]);
+                    if (in0 && s0 < sm.cnt[0] && s0 < Lim<KW>::ELEMS) sm.buf[s0] = cv[u];
+                    if (in1 && s1 < sm.cnt[1] && off1 + s1 < Lim<KW>::ELEMS) sm.buf[off1 + s1] = cv[u];
+                }
+            }
+            __syncthreads();
+            const bool consistent = sm.cnt[0] > 0 && sm.want[0] == sm.cnt[0] &&
+                                    (same || (sm.cnt[1] > 0 && sm.want[1] == sm.cnt[1])) &&
+                                    sm.cnt[0] + (same ? 0 : sm.cnt[1]) <= Lim<KW>::ELEMS;
+            const bool small = sm.cnt[0] <= WARP_SELECT_MAX && (same || sm.cnt[1] <= WARP_SELECT_MAX);
+            if (consistent && small) {
+                // two warps select the two pivots concurrently
+                if (warp < 2) {
+                    const u32 t = warp;
+                    const u32 region = (t == 1 && !same) ? 1 : 0;
+                    const ct* base = sm.buf + (region ? off1 : 0);
+                    const u32 rk = (t == 0 ? rl : rr) - sm.base[region];
+                    const ct res = warp_select_rank<KW>(base, sm.cnt[region], rk, sm.whist[t]);
+                    if (lane == 0) sm.wres[t] = res;
+                }
+                __syncthreads();
+                if (jl >= 0) pl = sm.wres[0];
+                if (jr <= top) pr = sm.wres[1];
+            } else if (consistent) {
+                if (same) {
+                    const u32 rk[2] = {rl - sm.base[0], rr - sm.base[0]};
+                    block_select_ranks<KW, 2>(sm.buf, sm.cnt[0], rk, sm.rs2);
+                    if (jl >= 0) pl = sm.rs2.result[0];
+                    if (jr <= top) pr = sm.rs2.result[1];
+                } else {
+                    const u32 rk0[1] = {rl - sm.base[0]};
+                    block_select_ranks<KW, 1>(sm.buf, sm.cnt[0], rk0, sm.rs1);
+                    if (jl >= 0) pl = sm.rs1.result[0];
+                    const u32 rk1[1] = {rr - sm.base[1]};
+                    block_select_ranks<KW, 1>(sm.buf + off1, sm.cnt[1], rk1, sm.rs1);
+                    if (jr <= top) pr = sm.rs1.result[0];
+                }
+            } else if (tid == 0) {
+                g->overflows++; // histogram and sample disagree: fall back to collecting the window
+            }
+        }
+        if (tid == 0) {
+            g->pl = (u128)pl;
+            g->pr = (u128)pr;
+            g->dst = s.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
+            g->cnt_a = 0;
+            g->cnt_b = 0;
+            g->pending = 1;
+            g->level = s.level + 1;
+            g->levels_grid++;
+            if (s.level == 0) g->sample_kept = kept;
+            // many a-elements expected: the pass compacts with block scans
+            g->dense = (jl >= 0 && kept > 0 && (double)(jl + 1) > (double)kept / 16.0) ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    for (u32 i = tid; i < HIST_BINS; i += PIV_NT) a.hist[i] = 0;
+    if (tid == 0) *a.samp_count = 0;
 }
 
-// First level: the source is always the input, so this variant carries no
-// candidate-source code (fewer registers on the pass that reads all n keys).
-template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass_first(SelArgs a) {
-    __shared__ PassSmem<PASS_NT> ps;
-    const SelState s = *a.st;
-    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
-    run_pass<PASS_NT, DT, true>(a, s, blockIdx.x, gridDim.x, ps);
-}
+// ---- partition + reduction + branch (whole grid)
 
-// First level, 16-byte-aligned input: a producer warp streams full tiles
-// into a ring of shared-memory stages with bulk (TMA) copies while 8 consumer
-// warps classify and compact, so HBM reads continue through the consumers'
-// barriers.  Every wait is bounded; a timeout latches TOPK_ETIMEOUT and the
-// block winds down without hanging.
-constexpr int TMA_CONS = 256;
-constexpr int TMA_NT = TMA_CONS + 32;
-constexpr u64 WAIT_LIMIT_NS = 200ull * 1000 * 1000;
-
-template <int DT> struct TmaCfg {
-    static constexpr u32 W = sizeof(typename Key<DT>::raw_t);
-    static constexpr u32 TILE = TMA_CONS * 16; // elements per stage
-    static constexpr u32 BYTES = TILE * W;     // 8, 16 or 32 KiB
-    static constexpr u32 STAGES = W == 2 ? 8 : W == 4 ? 6 : 3;
-    static constexpr u32 SMEM = STAGES * BYTES;
-};
-
-template <int DT, bool HAS_A, bool EXACT>
-__device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
-                            uint64_t* empty, u64 my_n, u32* dead, PassSmem<TMA_CONS>& ps) {
-    typedef Key<DT> K;
-    typedef typename K::raw_t raw_t;
-    typedef typename K::key_t key_t;
-    typedef Comp<K::KW> C;
-    typedef typename C::t ct;
-    typedef TmaCfg<DT> Cfg;
-    typedef SyncNamed<1, TMA_CONS> Sync;
+template <int DT>
+__device__ __forceinline__ Sink<DT> make_sink(const SelArgs& a, const SelState& s) {
+    typedef typename Key<DT>::raw_t raw_t;
+    typedef typename Key<DT>::key_t key_t;
     Sink<DT> sink;
     sink.out_keys = static_cast<raw_t*>(a.out_keys);
     sink.out_idx = a.out_idx;
@@ -91,12 +348,96 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
     sink.cap_b = a.cap_b;
     sink.cnt_a = &a.st->cnt_a;
     sink.cnt_b = &a.st->cnt_b;
+    return sink;
+}
+
+// Register-path pass (later levels; a first level on misaligned input).
+template <int DT, bool INPUT_ONLY> __device__ void grid_pass(const SelArgs& a, const SelState& s) {
+    typedef Key<DT> K;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    __shared__ PassSmem<PASS_NT> ps;
+    __shared__ WarpQ<KW> wq[PASS_NT / 32];
+    const Sink<DT> sink = make_sink<DT>(a, s);
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
+    const bool dense = s.dense != 0, exact = lo != (ct)0, has_a = pl > lo;
+    WarpQ<KW>& q = wq[threadIdx.x >> 5];
+    if (INPUT_ONLY || s.src == SRC_INPUT) {
+        const InputSrc<DT> src = InputSrc<DT>::make(a.keys, s.m_src);
+        if (!dense) pass_tiles_sparse<PASS_NT, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, q);
+        else if (exact) pass_tiles<PASS_NT, true, true, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+        else if (has_a) pass_tiles<PASS_NT, true, false, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+        else pass_tiles<PASS_NT, false, false, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+    } else if constexpr (!INPUT_ONLY) {
+        const CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
+        if (!dense) pass_tiles_sparse<PASS_NT, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, q);
+        else if (exact) pass_tiles<PASS_NT, true, true, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+        else if (has_a) pass_tiles<PASS_NT, true, false, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+        else pass_tiles<PASS_NT, false, false, DT>(src, blockIdx.x, gridDim.x, lo, pl, pr, sink, ps);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) pass_epilogue(a);
+}
+
+// First level: the source is always the input, so this variant carries no
+// candidate-source code (fewer registers on the pass that reads all n keys).
+template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass_first(SelArgs a) {
+    const SelState s = *a.st;
+    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
+    grid_pass<DT, true>(a, s);
+}
+
+template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass(SelArgs a) {
+    const SelState s = *a.st;
+    if (s.phase != PH_RUN || !s.pending) return;
+    grid_pass<DT, false>(a, s);
+}
+
+// First level, 16-byte-aligned input: a producer warp streams full tiles
+// into a ring of shared-memory stages with bulk (TMA) copies while 8 consumer
+// warps classify and compact, so HBM reads never wait for the compute.  Every
+// wait is bounded; a timeout latches TOPK_ETIMEOUT and the block winds down
+// without hanging.
+constexpr int TMA_CONS = 256;
+constexpr int TMA_NT = TMA_CONS + 32;
+constexpr u64 WAIT_LIMIT_NS = 200ull * 1000 * 1000;
+
+// Ring geometry.  A sparse pass is memory-bound: a deep ring, 2 blocks per
+// SM.  A dense pass is issue-bound: a shallower ring so that 3 blocks (24
+// consumer warps) fit on an SM.
+template <int DT, bool DENSE = false> struct TmaCfg {
+    static constexpr u32 W = sizeof(typename Key<DT>::raw_t);
+    static constexpr u32 TILE = TMA_CONS * 16; // elements per stage
+    static constexpr u32 BYTES = TILE * W;     // 8, 16 or 32 KiB
+    static constexpr u32 STAGES = DENSE ? (W == 2 ? 6 : W == 4 ? 3 : 2) : (W == 2 ? 8 : W == 4 ? 5 : 3);
+    static constexpr u32 SMEM = STAGES * BYTES;
+    static constexpr int MIN_BLOCKS = DENSE ? 3 : 1;
+};
+
+// MODE: 0 sparse (warp queues), 1 dense, 2 dense with a narrowed window.
+template <int DT, int MODE>
+__device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
+                            uint64_t* empty, u64 my_n, u32* dead, PassSmem<TMA_CONS>& ps, WarpQ<Key<DT>::KW>& wq) {
+    typedef Key<DT> K;
+    typedef typename K::key_t key_t;
+    typedef Comp<K::KW> C;
+    typedef typename C::t ct;
+    typedef TmaCfg<DT> Cfg;
+    typedef SyncNamed<1, TMA_CONS> Sync;
+    const Sink<DT> sink = make_sink<DT>(a, s);
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
     const u32 lane = lane_id();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0: input is 16-byte aligned
+    u32 nq = 0;
+    u32 ring = 0, ring_par = 0;
     for (u64 i = 0; i < my_n; ++i) {
-        const u32 stg = (u32)(i % Cfg::STAGES);
-        const u32 parity = (u32)((i / Cfg::STAGES) & 1);
+        const u32 stg = ring, parity = ring_par;
+        if (++ring == Cfg::STAGES) {
+            ring = 0;
+            ring_par ^= 1u;
+        }
         bool ok = !*(volatile u32*)dead;
         if (ok && !mbar_wait_bounded(&full[stg], parity, WAIT_LIMIT_NS)) {
             ok = false;
@@ -116,31 +457,235 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
         if (ok && lane == 0) mbar_arrive(&empty[stg]); // stage may be refilled
         const u64 tb = (blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE;
         auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
-        classify_emit<TMA_CONS, HAS_A, EXACT, Sync>(kk, pos, ok ? 0xFFFFu : 0u, lo, pl, pr, sink, ps);
+        const u32 valid = ok ? 0xFFFFu : 0u;
+        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, nq);
+        else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
     }
     // the ragged last tile, read directly by the block that owns it
     const u64 nfull = s.m_src / Cfg::TILE;
     if (s.m_src % Cfg::TILE != 0 && nfull % gridDim.x == blockIdx.x) {
-        const InputSrc<DT> src = InputSrc<DT>::make(a.keys, s.m_src);
         key_t kk[16];
         u32 ii[16];
         const u64 tb = nfull * (u64)Cfg::TILE;
-        const u32 valid = src.template load16<TMA_CONS>(tb, kk, ii);
-        auto pos = [&](int q) -> u32 { return src.template idx_of<TMA_CONS>(tb, q); };
-        classify_emit<TMA_CONS, HAS_A, EXACT, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
+        const u32 valid = isrc.template load16<TMA_CONS>(tb, kk, ii);
+        auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
+        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, nq);
+        else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
+    }
+    if (MODE == 0 && __any_sync(0xffffffffu, nq)) flush_hits<DT>(wq, nq, sink, lo, pl, pr);
+}
+
+// r[q] for a lane-dependent q without dynamic register indexing (which would
+// move r to local memory): a tree of selects.
+template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) {
+    T l1[8], l2[4], l3[2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) l1[j] = (q & 1u) ? r[2 * j + 1] : r[2 * j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) l2[j] = (q & 2u) ? l1[2 * j + 1] : l1[2 * j];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) l3[j] = (q & 4u) ? l2[2 * j + 1] : l2[2 * j];
+    return (q & 8u) ? l3[1] : l3[0];
+}
+
+// Dense levels (most elements in a): output room is reserved per tile with
+// one atomic per class, but the reservation of tile i is issued before the
+// elements of tile i-1 are written, so its latency overlaps real work.  Tile
+// i-1 is re-read from its shared-memory stage (held until then), and its
+// elements are staged per warp in shared memory so that the output is written
+// with fully coalesced stores.  Two threads take turns issuing the atomics so
+// that neither ever waits on its own pending result.
+struct DenseSmem {
+    u32 wa[2][TMA_CONS / 32], wb[2][TMA_CONS / 32]; // per-warp counts, by tile parity
+    u64 oa[2][TMA_CONS / 32], ob[2][TMA_CONS / 32]; // per-warp offsets inside the tile
+    u64 ba[2], bb[2];                               // tile bases in the output / candidates
+};
+
+template <int DT, bool EXACT>
+__device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
+                                  uint64_t* empty, u64 my_n, u32* dead, DenseSmem& ds, PassSmem<TMA_CONS>& ps,
+                                  WarpQ<Key<DT>::KW>& st) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    typedef Comp<K::KW> C;
+    typedef typename C::t ct;
+    typedef TmaCfg<DT, true> Cfg;
+    typedef SyncNamed<1, TMA_CONS> Sync;
+    constexpr int EPV = InputSrc<DT>::EPV, NV = InputSrc<DT>::NV;
+    constexpr u32 STRIDE = TMA_CONS * EPV; // index distance between a thread's vectors
+    const Sink<DT> sink = make_sink<DT>(a, s);
+    const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
+    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0
+    u32 ma_prev = 0, mb_prev = 0, stg_prev = 0, ib_prev = 0;
+    bool ok_prev = false;
+    u64 my_ra = 0, my_rb = 0; // pending reservation of the issuing thread
+    u32 ring = 0, ring_par = 0;   // stage and phase parity of tile i
+    for (u64 i = 0; i <= my_n; ++i) {
+        const bool cur = i < my_n, have_prev = i > 0;
+        const u32 par = (u32)(i & 1), ppar = par ^ 1u;
+        u32 ma = 0, mb = 0, stg = 0, ib = 0;
+        bool ok = false;
+        if (cur) {
+            stg = ring;
+            const u32 fpar = ring_par;
+            if (++ring == Cfg::STAGES) {
+                ring = 0;
+                ring_par ^= 1u;
+            }
+            ok = !*(volatile u32*)dead;
+            if (ok && !mbar_wait_bounded(&full[stg], fpar, WAIT_LIMIT_NS)) {
+                ok = false;
+                *(volatile u32*)dead = 1;
+                if (lane == 0) latch(a.err, ST_ETIMEOUT);
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            // position of slot q = ib + (q / EPV) * STRIDE + q % EPV (32-bit: positions < 2^32)
+            ib = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE) + threadIdx.x * EPV;
+            if (ok) {
+                key_t kk[16];
+                InputSrc<DT>::template load16_smem<TMA_CONS>(
+                    reinterpret_cast<const uint4*>(stages + (size_t)stg * Cfg::BYTES), kk);
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const ct c = C::make(kk[q], ib + (u32)((q / EPV) * STRIDE + q % EPV));
+                    const bool lt = c < pl;
+                    ma |= (u32)(lt && (!EXACT || c >= lo)) << q;
+                    mb |= (u32)(!lt && c <= pr) << q;
+                }
+            }
+            const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
+            const u32 wb = __reduce_add_sync(0xffffffffu, (u32)__popc(mb));
+            if (lane == 0) {
+                ds.wa[par][warp] = wa;
+                ds.wb[par][warp] = wb;
+            }
+        }
+        Sync::sync(); // counts of tile i in; writes of tile i-2 done
+        const u32 issuer_cur = par ? 32u : 0u, issuer_prev = ppar ? 32u : 0u;
+        if (have_prev && threadIdx.x == issuer_prev) {
+            ds.ba[ppar] = my_ra;
+            ds.bb[ppar] = my_rb;
+        }
+        if (cur && threadIdx.x == issuer_cur) {
+            u64 ta = 0, tb2 = 0;
+            for (int w = 0; w < TMA_CONS / 32; ++w) {
+                ds.oa[par][w] = ta;
+                ds.ob[par][w] = tb2;
+                ta += ds.wa[par][w];
+                tb2 += ds.wb[par][w];
+            }
+            my_ra = 0;
+            my_rb = 0;
+            if (ta) my_ra = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ta);
+            if (tb2) my_rb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)tb2);
+        }
+        Sync::sync(); // base of tile i-1 in
+        if (have_prev && ok_prev) {
+            uint4 v[NV];
+            const uint4* stage = reinterpret_cast<const uint4*>(stages + (size_t)stg_prev * Cfg::BYTES);
+#pragma unroll
+            for (int j = 0; j < NV; ++j) v[j] = stage[j * TMA_CONS + threadIdx.x];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[stg_prev]); // keys are in registers: stage may be refilled
+            raw_t rr[16];
+            InputSrc<DT>::unpack_raw(v, rr);
+            // a-elements: every thread appends its own to the warp's staging
+            // area at an offset from one warp scan (both halves packed in one
+            // word), then the warp writes them out with coalesced stores.
+            u64 xa = ds.ba[ppar] + ds.oa[ppar][warp];
+            {
+                const u32 cnt = (u32)__popc(ma_prev & 0xFFu) | ((u32)__popc(ma_prev >> 8) << 16);
+                u32 incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (u32)o) incl += y;
+                }
+                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+                const u32 excl = incl - cnt;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u32 n = h ? (tot >> 16) : (tot & 0xFFFFu);
+                    u32 o = h ? (excl >> 16) : (excl & 0xFFFFu);
+                    const u32 dummy = WarpQ<Key<DT>::KW>::QCAP + lane; // absorbs unselected slots
+#pragma unroll
+                    for (int q = 8 * h; q < 8 * h + 8; ++q) {
+                        const u32 bit = (ma_prev >> q) & 1u;
+                        const u32 d = bit ? o : dummy;
+                        st.k[d] = (key_t)rr[q];
+                        st.i[d] = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
+                        o += bit;
+                    }
+                    __syncwarp();
+                    sink.copy_a(xa, st.k, st.i, n);
+                    __syncwarp();
+                    xa += n;
+                }
+            }
+            if (__any_sync(0xffffffffu, mb_prev)) { // b is sparse: visit set bits only
+                u64 xb = ds.bb[ppar] + ds.ob[ppar][warp];
+                const u32 cnt = (u32)__popc(mb_prev & 0xFFu) | ((u32)__popc(mb_prev >> 8) << 16);
+                u32 incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (u32)o) incl += y;
+                }
+                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+                const u32 excl = incl - cnt;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const u32 n = h ? (tot >> 16) : (tot & 0xFFFFu);
+                    u32 o = h ? (excl >> 16) : (excl & 0xFFFFu);
+                    u32 m = (mb_prev >> (8 * h)) & 0xFFu;
+                    while (m) {
+                        const u32 q = (u32)(__ffs(m) - 1) + 8u * h;
+                        m &= m - 1;
+                        st.k[o] = K::fwd(pick16(rr, q));
+                        st.i[o] = ib_prev + (q / EPV) * STRIDE + q % EPV;
+                        ++o;
+                    }
+                    __syncwarp();
+                    sink.copy_b(xb, st.k, st.i, n);
+                    __syncwarp();
+                    xb += n;
+                }
+            }
+        }
+        ma_prev = ma;
+        mb_prev = mb;
+        stg_prev = stg;
+        ib_prev = ib;
+        ok_prev = ok;
+    }
+    // the ragged last tile, read directly by the block that owns it
+    const u64 nfull = s.m_src / Cfg::TILE;
+    if (s.m_src % Cfg::TILE != 0 && nfull % gridDim.x == blockIdx.x) {
+        key_t kk[16];
+        u32 ii[16];
+        const u64 tb = nfull * (u64)Cfg::TILE;
+        const u32 valid = isrc.template load16<TMA_CONS>(tb, kk, ii);
+        auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
+        classify_emit<TMA_CONS, true, EXACT, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
     }
 }
 
-template <int DT> __global__ void __launch_bounds__(TMA_NT) k_pass_tma(SelArgs a) {
-    typedef TmaCfg<DT> Cfg;
+template <int DT, bool DENSE>
+__global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pass_tma(SelArgs a) {
+    typedef TmaCfg<DT, DENSE> Cfg;
     typedef typename Key<DT>::raw_t raw_t;
+    constexpr int KW = Key<DT>::KW;
     extern __shared__ __align__(128) unsigned char stages[];
     __shared__ __align__(8) uint64_t full[Cfg::STAGES];
     __shared__ __align__(8) uint64_t empty[Cfg::STAGES];
     __shared__ PassSmem<TMA_CONS> ps;
+    __shared__ WarpQ<KW> wq[TMA_CONS / 32];
+    __shared__ DenseSmem ds;
     __shared__ u32 dead;
     const SelState s = *a.st;
-    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
+    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT || (s.dense != 0) != DENSE) return;
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < Cfg::STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -155,10 +700,10 @@ template <int DT> __global__ void __launch_bounds__(TMA_NT) k_pass_tma(SelArgs a
     if (threadIdx.x >= TMA_CONS) { // producer warp: one lane issues the copies
         if (threadIdx.x == TMA_CONS) {
             const raw_t* keys = static_cast<const raw_t*>(a.keys);
+            u32 stg = 0, epar = 1; // the first pass over the ring waits for nothing
             for (u64 i = 0; i < my_n; ++i) {
-                const u32 stg = (u32)(i % Cfg::STAGES);
                 if (i >= Cfg::STAGES) {
-                    const u32 parity = (u32)(((i / Cfg::STAGES) - 1) & 1);
+                    const u32 parity = epar;
                     if (*(volatile u32*)&dead || !mbar_wait_bounded(&empty[stg], parity, WAIT_LIMIT_NS)) {
                         *(volatile u32*)&dead = 1;
                         latch(a.err, ST_ETIMEOUT);
@@ -168,32 +713,32 @@ template <int DT> __global__ void __launch_bounds__(TMA_NT) k_pass_tma(SelArgs a
                 const u64 t = blockIdx.x + i * gridDim.x;
                 mbar_arrive_expect_tx(&full[stg], Cfg::BYTES);
                 bulk_g2s(stages + (size_t)stg * Cfg::BYTES, keys + t * Cfg::TILE, Cfg::BYTES, &full[stg]);
+                if (++stg == Cfg::STAGES) {
+                    stg = 0;
+                    epar ^= 1u;
+                }
             }
         }
         return;
     }
-    typedef Comp<Key<DT>::KW> C;
+    typedef Comp<KW> C;
     typedef typename C::t ct;
-    const ct lo = C::from128(s.lo), pl = C::from128(s.pl);
-    if (lo != (ct)0) tma_consume<DT, true, true>(a, s, stages, full, empty, my_n, &dead, ps);
-    else if (pl > lo) tma_consume<DT, true, false>(a, s, stages, full, empty, my_n, &dead, ps);
-    else tma_consume<DT, false, false>(a, s, stages, full, empty, my_n, &dead, ps);
+    const ct lo = C::from128(s.lo);
+    WarpQ<KW>& q = wq[threadIdx.x >> 5];
+    if constexpr (!DENSE) tma_consume<DT, 0>(a, s, stages, full, empty, my_n, &dead, ps, q);
+    else if (lo != (ct)0) tma_consume_dense<DT, true>(a, s, stages, full, empty, my_n, &dead, ds, ps, q);
+    else tma_consume_dense<DT, false>(a, s, stages, full, empty, my_n, &dead, ds, ps, q);
+    SyncNamed<1, TMA_CONS>::sync();
+    if (threadIdx.x == 0) pass_epilogue(a);
 }
 
-template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass(SelArgs a) {
-    __shared__ PassSmem<PASS_NT> ps;
-    const SelState s = *a.st;
-    if (s.phase != PH_RUN || !s.pending) return;
-    run_pass<PASS_NT, DT>(a, s, blockIdx.x, gridDim.x, ps);
-}
-
+// Remaining levels in one block, then the exact finish.
 template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, int first) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<BlockSmem<Key<DT>::KW>*>(smem_raw);
     SelState* g = a.st;
     if (threadIdx.x == 0) {
         if (first) init_state<DT>(g, a);
-        else decide(*g);
         if (g->phase == PH_RUN) g->phase = PH_FINISH;
         sm.flag = g->phase == PH_FINISH;
     }
@@ -316,7 +861,7 @@ template <int KW> static Tuning make_tuning(const topk_params* prm, int sms) {
     tu.sample = p.sample_size ? std::min<u32>(std::max<u32>(p.sample_size, 64), ELEMS) : ELEMS;
     tu.parts = p.partitions ? p.partitions : (u32)sms;
     tu.T = p.finish_threshold ? std::min<u32>(std::max<u32>(p.finish_threshold, 64), ELEMS) : ELEMS;
-    tu.G = 4 * tu.T;
+    tu.G = tu.T; // grid levels run until the one-block finish can take over
     tu.z = p.delta_factor > 0.f ? p.delta_factor : 4.0f;
     tu.flags = p.flags;
     tu.seed = p.seed ? p.seed : 0x243F6A8885A308D3ull;
@@ -364,11 +909,14 @@ template <int DT> static topk_status set_smem_attrs() {
     if (cudaGetDevice(&dev) != cudaSuccess) return TOPK_ECUDA;
     const uint64_t bit = 1ull << (dev & 63);
     if (done_mask.load() & bit) return TOPK_OK;
-    if (cudaFuncSetAttribute(k_pass_tma<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TmaCfg<DT>::SMEM) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_pass_tma<DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TmaCfg<DT, false>::SMEM) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pass_tma<DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TmaCfg<DT, true>::SMEM) != cudaSuccess)
         return TOPK_ECUDA;
     const int bytes = (int)sizeof(BlockSmem<Key<DT>::KW>);
-    if (cudaFuncSetAttribute(k_plan<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_pivots<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PivotSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
     if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return TOPK_ECUDA;
@@ -377,12 +925,12 @@ template <int DT> static topk_status set_smem_attrs() {
 }
 
 // Resident blocks per SM of each pass variant: the grid is one full wave.
-template <int DT> static int tma_grid(int sms) {
+template <int DT, bool DENSE> static int tma_grid(int sms) {
     static int occ = 0;
     if (occ == 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pass_tma<DT>, TMA_NT, TmaCfg<DT>::SMEM) !=
-            cudaSuccess)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_pass_tma<DT, DENSE>, TMA_NT,
+                                                          TmaCfg<DT, DENSE>::SMEM) != cudaSuccess)
             o = 1;
         occ = std::max(1, o);
     }
@@ -441,17 +989,22 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
         }
     }
     const size_t smem = sizeof(BlockSmem<KW>);
+    const int smp_blocks = (int)((tu.sample * SMP_MAX_SCALE + SMP_NT * SMP_DRAWS - 1) / (SMP_NT * SMP_DRAWS));
     for (int l = 0; l < levels; ++l) {
-        k_plan<DT><<<1, BLK_NT, smem, st>>>(a, l == 0 ? 1 : 0);
+        k_sample<DT><<<smp_blocks, SMP_NT, 0, st>>>(a, l == 0 ? 1 : 0);
+        k_pivots<DT><<<1, PIV_NT, sizeof(PivotSmem<KW>), st>>>(a, l == 0 ? 1 : 0);
         if (l == 0 && ctx) profile_pass_begin(ctx, st);
-        if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY))
-            k_pass_tma<DT><<<tma_grid<DT>(sms), TMA_NT, TmaCfg<DT>::SMEM, st>>>(a);
+        if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY)) {
+            // the mode is chosen on the device: the variant that does not match returns at once
+            k_pass_tma<DT, false><<<tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st>>>(a);
+            k_pass_tma<DT, true><<<tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st>>>(a);
+        }
         else if (l == 0) k_pass_first<DT><<<pass_grid<DT>(sms, true), PASS_NT, 0, st>>>(a);
         else k_pass<DT><<<pass_grid<DT>(sms, false), PASS_NT, 0, st>>>(a);
         if (l == 0 && ctx) profile_pass_end(ctx, st);
     }
     k_finish<DT><<<1, BLK_NT, smem, st>>>(a, levels == 0 ? 1 : 0);
-    if (ctx) count_launch(ctx, 2 * (uint64_t)levels + 1);
+    if (ctx) count_launch(ctx, 3 * (uint64_t)levels + 1 + (levels > 0 && a.aligned ? 1 : 0));
     return cuda_status(cudaGetLastError());
 }
 
@@ -470,11 +1023,17 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
     const size_t kbytes = KW / 8;
     Carve cv;
     const size_t off_part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)ctx->sms * EXT_BLOCKS_PER_SM);
+    const size_t off_samp = cv.take(sizeof(typename Comp<KW>::t) * (size_t)Lim<KW>::ELEMS);
     const size_t off_k0 = cv.take(cap * kbytes), off_k1 = cv.take(cap * kbytes);
     const size_t off_i0 = cv.take(cap * 4), off_i1 = cv.take(cap * 4);
     topk_status rs = ensure_scratch(ctx, cv.off);
     if (rs != TOPK_OK) return rs;
     char* base = static_cast<char*>(ctx->scratch.base);
+    a.samp = base + off_samp;
+    a.samp_cap = Lim<KW>::ELEMS;
+    a.samp_count = ctx->d_counter + 3;
+    a.pass_done = ctx->d_counter + 2;
+    a.hist = ctx->d_hist;
     a.cand_key[0] = base + off_k0;
     a.cand_key[1] = base + off_k1;
     a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
@@ -494,11 +1053,14 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
 constexpr u64 NOALLOC_MAX_N = 1ull << 22;  // largest n accepted (4 Mi keys)
 constexpr u64 NOALLOC_CAP = 1ull << 18;    // candidate pairs per buffer
 constexpr size_t NA_OFF_STATE = 0;         // SelState
-constexpr size_t NA_OFF_WORDS = 4096;      // [0] error word, [1] block-done counter
-constexpr size_t NA_OFF_PART = 8192;       // per-block composites of the k = 1 / k = n reduction
+constexpr size_t NA_OFF_WORDS = 4096;      // [0] error, [1] reduction done, [2] pass done, [3] sample count
+constexpr size_t NA_OFF_HIST = 8192;       // HIST_BINS u32
+constexpr size_t NA_OFF_PART = NA_OFF_HIST + HIST_BINS * 4; // per-block composites of the k = 1 / k = n reduction
 constexpr size_t NA_PART_BYTES = 64 * 1024;
-constexpr size_t NA_OFF_CAND = NA_OFF_PART + NA_PART_BYTES;
-constexpr size_t NA_BYTES = NA_OFF_CAND + 2 * NOALLOC_CAP * (8 + 4); // about 6 MiB
+constexpr size_t NA_OFF_SAMP = NA_OFF_PART + NA_PART_BYTES; // sample, Lim<32>::ELEMS * 8 = Lim<64>::ELEMS * 16 bytes
+constexpr size_t NA_SAMP_BYTES = 128 * 1024;
+constexpr size_t NA_OFF_CAND = NA_OFF_SAMP + NA_SAMP_BYTES;
+constexpr size_t NA_BYTES = NA_OFF_CAND + 2 * NOALLOC_CAP * (8 + 4); // about 6.2 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
@@ -539,8 +1101,16 @@ static topk_status run_select_noalloc(char* base, int sms, const void* keys, u64
     a.cand_key[1] = cand + NOALLOC_CAP * 8;
     a.cand_idx[0] = reinterpret_cast<u32*>(cand + 2 * NOALLOC_CAP * 8);
     a.cand_idx[1] = reinterpret_cast<u32*>(cand + 2 * NOALLOC_CAP * 8 + NOALLOC_CAP * 4);
-    // the error word and the block-done counter must start at zero
-    if (cudaMemsetAsync(words, 0, 2 * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
+    static_assert(sizeof(typename Comp<KW>::t) * Lim<KW>::ELEMS <= NA_SAMP_BYTES, "sample region too small");
+    a.samp = base + NA_OFF_SAMP;
+    a.samp_cap = Lim<KW>::ELEMS;
+    a.pass_done = words + 2;
+    a.samp_count = words + 3;
+    a.hist = reinterpret_cast<u32*>(base + NA_OFF_HIST);
+    // the error word, the block-done counters, the sample count and the
+    // histogram must start at zero (a call that failed may have left them set)
+    if (cudaMemsetAsync(words, 0, 4 * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
+    if (cudaMemsetAsync(a.hist, 0, HIST_BINS * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
     if (d_status && cudaMemsetAsync(d_status, 0, sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
     return enqueue_select<DT>(nullptr, a, tu, sms, words + 1, base + NA_OFF_PART, st);
 }

@@ -28,6 +28,7 @@ template <int KW> struct BlockSmem {
     PassSmem<BLK_NT> ps;
     u32 kept;
     u32 flag;
+    long long jl, jr;
 };
 
 __device__ inline void latch(u32* err, u32 code) { atomicCAS(err, 0u, code); }
@@ -137,8 +138,15 @@ template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>
             kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
         }
         if (kept > 0) {
-            long long jl, jr;
-            pivot_ranks(kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+            // pivot ranks once (FP64 is slow on this part; the block shares them)
+            if (threadIdx.x == 0) {
+                long long l, r;
+                pivot_ranks(kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, l, r);
+                sm.jl = l;
+                sm.jr = r;
+            }
+            __syncthreads();
+            const long long jl = sm.jl, jr = sm.jr;
             const long long top = (long long)kept - 1;
             const u32 r[2] = {(u32)(jl < 0 ? 0 : jl > top ? top : jl), (u32)(jr < 0 ? 0 : jr > top ? top : jr)};
             block_select_ranks<KW, 2>(sm.samp, kept, r, sm.rs2);

@@ -78,6 +78,24 @@ template <int DT> struct InputSrc {
         }
     }
 
+    // Raw key words of the NV 16-byte vectors, in slot order.
+    __device__ __forceinline__ static void unpack_raw(const uint4 (&v)[NV], raw_t (&rr)[16]) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+#pragma unroll
+            for (int i = 0; i < EPV; ++i) {
+                if (sizeof(raw_t) == 4) {
+                    rr[j * EPV + i] = (raw_t)u4get(v[j], i);
+                } else if (sizeof(raw_t) == 2) {
+                    const u32 w = u4get(v[j], i >> 1);
+                    rr[j * EPV + i] = (raw_t)((i & 1) ? (w >> 16) : (w & 0xFFFFu));
+                } else {
+                    rr[j * EPV + i] = (raw_t)(((u64)u4get(v[j], 2 * i + 1) << 32) | u4get(v[j], 2 * i));
+                }
+            }
+        }
+    }
+
     // 16 elements per thread from a tile staged in shared memory.
     template <int NT>
     __device__ __forceinline__ static void load16_smem(const uint4* stage, key_t (&kk)[16]) {
@@ -256,6 +274,41 @@ template <int DT> struct Sink {
             out_idx[out_base + pos] = x;
         }
     }
+    // a-element given by its raw key bits
+    __device__ __forceinline__ void put_a_raw(u64 pos, raw_t r, u32 x) const {
+        if (pos < cap_a) {
+            out_keys[out_base + pos] = r;
+            out_idx[out_base + pos] = x;
+        }
+    }
+    // n staged a-elements (raw keys) to output positions pos..pos+n-1 (all
+    // lanes of a warp call; coalesced)
+    template <class QK>
+    __device__ __forceinline__ void copy_a(u64 pos, const QK* sk, const u32* si, u32 n) const {
+        if (pos + n <= cap_a) {
+            raw_t* ok = out_keys + out_base + pos;
+            u32* oi = out_idx + out_base + pos;
+            for (u32 e = lane_id(); e < n; e += 32) {
+                ok[e] = (raw_t)sk[e];
+                oi[e] = si[e];
+            }
+        } else {
+            for (u32 e = lane_id(); e < n; e += 32) put_a_raw(pos + e, (raw_t)sk[e], si[e]);
+        }
+    }
+    template <class QK>
+    __device__ __forceinline__ void copy_b(u64 pos, const QK* sk, const u32* si, u32 n) const {
+        if (pos + n <= cap_b) {
+            key_t* bk = ck + pos;
+            u32* bi = ci + pos;
+            for (u32 e = lane_id(); e < n; e += 32) {
+                bk[e] = (key_t)sk[e];
+                bi[e] = si[e];
+            }
+        } else {
+            for (u32 e = lane_id(); e < n; e += 32) put_b(pos + e, (key_t)sk[e], si[e]);
+        }
+    }
     __device__ __forceinline__ void put_b(u64 pos, key_t k, u32 x) const {
         if (pos < cap_b) {
             ck[pos] = k;
@@ -387,6 +440,120 @@ __device__ __forceinline__ void classify_emit(const KeyT (&kk)[16], PosF pos, u3
     }
 }
 
+// ------------------------------------------------- sparse compaction
+// When a and b are a small fraction of the source (every k except around
+// n/2), a warp needs no block barrier: one pair comparison per element finds
+// the few elements that can be in a or b (pair <= pr); those are appended to
+// the warp's own shared-memory queue, which is classified exactly and flushed
+// to the output / candidate buffer with one atomic per class per QCAP hits.
+
+template <int KW> struct WarpQ {
+    static constexpr int QCAP = 256;
+    typename Comp<KW>::key_t k[QCAP + 32]; // + one scratch entry per lane for
+    u32 i[QCAP + 32];                      //   branch-free staging
+};
+
+// Classifies the n queued hits exactly on the pair and writes a-elements to
+// the output and b-elements to the candidate buffer, with one atomic per
+// class (all 32 lanes call).  Kept out of line: it runs rarely, and inlining
+// it into the streaming loop costs instruction-cache space on every tile.
+template <int DT>
+__device__ __noinline__ void flush_hits(WarpQ<Key<DT>::KW>& q, u32 n, const Sink<DT>& sink,
+                                        typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                        typename Comp<Key<DT>::KW>::t pr) {
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename C::t ct;
+    __syncwarp();
+    u32 ca = 0, cb = 0;
+    for (u32 e = lane_id(); e < n; e += 32) {
+        const ct c = C::make(q.k[e], q.i[e]);
+        if (c >= lo && c < pl) ++ca;
+        else if (c >= pl && c <= pr) ++cb;
+    }
+    ca = __reduce_add_sync(0xffffffffu, ca);
+    cb = __reduce_add_sync(0xffffffffu, cb);
+    u64 ba = 0, bb = 0;
+    if (lane_id() == 0) {
+        if (ca) ba = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ca);
+        if (cb) bb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)cb);
+    }
+    ba = __shfl_sync(0xffffffffu, (unsigned long long)ba, 0);
+    bb = __shfl_sync(0xffffffffu, (unsigned long long)bb, 0);
+    const u32 below = lanemask_lt();
+    for (u32 e0 = 0; e0 < n; e0 += 32) {
+        const u32 e = e0 + lane_id();
+        bool isa = false, isb = false;
+        typename C::key_t kv = 0;
+        u32 iv = 0;
+        if (e < n) {
+            kv = q.k[e];
+            iv = q.i[e];
+            const ct c = C::make(kv, iv);
+            isa = c >= lo && c < pl;
+            isb = c >= pl && c <= pr;
+        }
+        const u32 bala = __ballot_sync(0xffffffffu, isa), balb = __ballot_sync(0xffffffffu, isb);
+        if (isa) sink.put_a(ba + __popc(bala & below), kv, iv);
+        if (isb) sink.put_b(bb + __popc(balb & below), kv, iv);
+        ba += __popc(bala);
+        bb += __popc(balb);
+    }
+    __syncwarp();
+}
+
+// One tile in sparse mode (all 32 lanes call; no block-wide barrier).  Every
+// element with pair <= pr (the only ones that can be in a or b) is queued.
+template <int DT, class CT, class KeyT, class PosF>
+__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
+                                                const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, u32& nq) {
+    typedef Comp<Key<DT>::KW> C;
+    u32 hit = 0;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
+    hit &= valid;
+    if (!__any_sync(0xffffffffu, hit)) return;
+    const u32 below = lanemask_lt();
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+        const u32 bal = __ballot_sync(0xffffffffu, (hit >> s) & 1u);
+        if (bal) {
+            if (nq + 32 > (u32)WarpQ<Key<DT>::KW>::QCAP) {
+                flush_hits<DT>(q, nq, sink, lo, pl, pr);
+                nq = 0;
+            }
+            if ((hit >> s) & 1u) {
+                const u32 slot = nq + __popc(bal & below);
+                q.k[slot] = kk[s];
+                q.i[slot] = pos(s);
+            }
+            nq += __popc(bal);
+        }
+    }
+}
+
+// Register path in sparse mode.
+template <int NT, int DT, class Src>
+__device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, typename Comp<Src::KW>::t lo,
+                                  typename Comp<Src::KW>::t pl, typename Comp<Src::KW>::t pr, const Sink<DT>& sink,
+                                  WarpQ<Key<DT>::KW>& q) {
+    typedef typename Src::key_t key_t;
+    constexpr u64 TILE = (u64)NT * 16;
+    const u64 ntiles = (src.extent() + TILE - 1) / TILE;
+    u32 nq = 0;
+    for (u64 t = tile0; t < ntiles; t += tile_step) {
+        key_t kk[16];
+        u32 ii[16];
+        const u64 tb = t * TILE;
+        const u32 valid = src.template load16<NT>(tb, kk, ii);
+        auto pos = [&](int s) -> u32 {
+            if constexpr (Src::IMPLICIT_IDX) return src.template idx_of<NT>(tb, s);
+            else return ii[s];
+        };
+        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, q, nq);
+    }
+    if (__any_sync(0xffffffffu, nq)) flush_hits<DT>(q, nq, sink, lo, pl, pr);
+}
+
 // Register path: every thread loads its 16 elements of each tile itself.
 template <int NT, bool HAS_A, bool EXACT, int DT, class Src>
 __device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
@@ -425,6 +592,7 @@ __device__ void pass_tiles(const Src& src, u64 tile0, u64 tile_step,
 
 template <int KW, int NTGT> struct RadixSmem {
     typedef typename Comp<KW>::t ct;
+    ct diff[32];
     u32 hist[NTGT][256];
     ct prefix[NTGT];
     ct mask[NTGT];
@@ -451,15 +619,42 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
     typedef Comp<KW> C;
     typedef typename C::t ct;
     const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    // Leading digits shared by every element need no pass: find the highest
+    // bit in which any element differs from the first one.
+    ct x = 0;
+    if (count > 0) {
+        const ct v0 = v[0];
+        for (u32 i = tid; i < count; i += blockDim.x) x |= v[i] ^ v0;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 lo64 = __shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)x, o);
+        ct y = (ct)lo64;
+        if (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
+        x |= y;
+    }
+    if (lane == 0) sm.diff[warp] = x;
+    __syncthreads();
+    ct diff = 0;
+    for (u32 w = 0; w < (blockDim.x >> 5); ++w) diff |= sm.diff[w];
+    constexpr int TOTAL = C::DIGITS * 8;
+    int d0 = C::DIGITS; // all equal: every target is v[0]
+    if (diff != 0) d0 = (TOTAL - bit_length_fast(diff)) / 8;
+    ct top = 0; // mask of the shared leading digits
+    if (d0 > 0) {
+        const int keep = 8 * (C::DIGITS - (d0 < C::DIGITS ? d0 : C::DIGITS));
+        top = (keep >= TOTAL) ? (ct)0 : (ct)(((ct)1 << TOTAL) - 1) & ~(ct)(((ct)1 << keep) - 1);
+        if (TOTAL == 64) top = keep >= 64 ? (ct)0 : (ct)(~(u64)0 << keep);
+    }
     if (tid < NTGT) {
-        sm.prefix[tid] = 0;
-        sm.mask[tid] = 0;
+        sm.prefix[tid] = count > 0 ? (v[0] & top) : (ct)0;
+        sm.mask[tid] = top;
         sm.rank[tid] = rank[tid];
-        sm.done[tid] = 0;
+        sm.done[tid] = d0 >= C::DIGITS;
         sm.unique[tid] = 0;
     }
     __syncthreads();
-    for (int d = 0; d < C::DIGITS; ++d) {
+    for (int d = d0; d < C::DIGITS; ++d) {
         bool all_done = true;
 #pragma unroll
         for (int t = 0; t < NTGT; ++t) all_done = all_done && sm.done[t];
@@ -553,6 +748,103 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
             if ((v[i] & msk) == pfx) sm.result[t] = v[i];
     }
     __syncthreads();
+}
+
+// Warp-level version for small sets: one warp selects the element of 0-based
+// rank `rank` among v[0..count) with its own 256-bin histogram in shared
+// memory (no block barrier, so several warps can select concurrently).
+template <int KW>
+__device__ typename Comp<KW>::t warp_select_rank(const typename Comp<KW>::t* v, u32 count, u32 rank, u32* hist) {
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    const u32 lane = lane_id();
+    const ct v0 = v[0];
+    ct x = 0;
+    for (u32 i = lane; i < count; i += 32) x |= v[i] ^ v0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ct y = (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)x, o);
+        if (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
+        x |= y;
+    }
+    if (x == 0) return v0; // all equal
+    constexpr int TOTAL = C::DIGITS * 8;
+    const int d0 = (TOTAL - bit_length_fast(x)) / 8;
+    ct mask = 0;
+    if (d0 > 0) {
+        const int keep = 8 * (C::DIGITS - d0);
+        mask = (TOTAL == 64) ? (ct)(~(u64)0 << keep) : (ct)((((ct)1 << TOTAL) - 1) & ~(((ct)1 << keep) - 1));
+    }
+    ct prefix = v0 & mask;
+    u32 r = rank;
+    for (int d = d0; d < C::DIGITS; ++d) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) hist[lane * 8 + j] = 0;
+        __syncwarp();
+        for (u32 i = lane; i < count; i += 32) {
+            const ct c = v[i];
+            if ((c & mask) == prefix) atomicAdd(&hist[C::digit(c, d)], 1u);
+        }
+        __syncwarp();
+        u32 h[8], sum = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            h[j] = hist[lane * 8 + j];
+            sum += h[j];
+        }
+        u32 incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += y;
+        }
+        const u32 excl = incl - sum;
+        u32 bin = 0, below = 0, hb = 0;
+        const bool mine = r >= excl && r < incl;
+        if (mine) {
+            u32 acc = excl;
+            int b = -1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (b < 0) {
+                    if (r < acc + h[j]) {
+                        b = j;
+                        hb = h[j];
+                    } else {
+                        acc += h[j];
+                    }
+                }
+            }
+            bin = lane * 8 + b;
+            below = acc;
+        }
+        const u32 src = __ffs(__ballot_sync(0xffffffffu, mine)) - 1;
+        bin = __shfl_sync(0xffffffffu, bin, src);
+        below = __shfl_sync(0xffffffffu, below, src);
+        hb = __shfl_sync(0xffffffffu, hb, src);
+        const int shift = (C::DIGITS - 1 - d) * 8;
+        prefix |= (ct)bin << shift;
+        mask |= (ct)0xFFu << shift;
+        r -= below;
+        __syncwarp();
+        if (hb == 1) { // the single element with this prefix
+            ct res = 0;
+            bool found = false;
+            for (u32 i = lane; i < count; i += 32) {
+                const ct c = v[i];
+                if ((c & mask) == prefix) {
+                    res = c;
+                    found = true;
+                }
+            }
+            const u32 who = __ffs(__ballot_sync(0xffffffffu, found)) - 1;
+            const u64 lo64 = __shfl_sync(0xffffffffu, (unsigned long long)(u64)res, who);
+            ct out = (ct)lo64;
+            if (sizeof(ct) > 8) out |= (ct)__shfl_sync(0xffffffffu, (unsigned long long)(u64)((u128)res >> 64), who) << 64;
+            return out;
+        }
+    }
+    return prefix;
 }
 
 // ------------------------------------------------------------- sampling

@@ -431,13 +431,9 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
     const u32 lane = lane_id();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0: input is 16-byte aligned
     u32 nq = 0;
-    u32 ring = 0, ring_par = 0;
     for (u64 i = 0; i < my_n; ++i) {
-        const u32 stg = ring, parity = ring_par;
-        if (++ring == Cfg::STAGES) {
-            ring = 0;
-            ring_par ^= 1u;
-        }
+        const u32 stg = (u32)(i % Cfg::STAGES);
+        const u32 parity = (u32)((i / Cfg::STAGES) & 1);
         bool ok = !*(volatile u32*)dead;
         if (ok && !mbar_wait_bounded(&full[stg], parity, WAIT_LIMIT_NS)) {
             ok = false;

@@ -197,6 +197,67 @@ topk_status topk_select_noalloc(const void *d_keys, uint64_t n, uint64_t k,
                                 void *d_kth_key, uint32_t *d_kth_idx, uint32_t *d_status,
                                 void *stream);
 
+/* ------------------------------------------------------------- serving
+ * A request loop over one GPU (no counterpart in the paper): requests are
+ * submitted without blocking, admitted in arrival order while the bytes they
+ * pin on the device (input + outputs + per-request state) stay within
+ * `hbm_budget`, and run concurrently on `max_slots` streams.  Waiting
+ * requests of at most 2^18 keys and the same key type are grouped into one
+ * batched launch as they arrive (continuous batching); larger ones run as
+ * single selections on their own stream.  Every request's result is the one
+ * topk_select returns for it alone.  Buffers are caller-owned and must stay
+ * valid until the request is done. */
+typedef struct topk_server topk_server;
+
+typedef struct {
+    const void *d_keys;    /* n keys of dtype */
+    uint64_t n, k;         /* 1 <= k <= n < 2^32 */
+    topk_dtype dtype;
+    void *d_out_keys;      /* k keys */
+    uint32_t *d_out_idx;   /* k positions */
+    void *d_kth_key;       /* 1 key */
+    uint32_t *d_kth_idx;   /* 1 position */
+    uint64_t arrival_ns;   /* scheduled arrival on topk_serve_now_ns()'s clock;
+                              0 = the time of submission */
+} topk_request;
+
+typedef struct {
+    uint64_t submitted, completed, rejected, failed;
+    uint64_t keys;          /* keys of completed requests */
+    uint64_t p50_ns, p99_ns, max_ns; /* latency = completion - arrival */
+    uint64_t batches;       /* batched launches */
+    uint64_t batched_requests;
+    uint64_t peak_inflight_bytes;
+    double elapsed_s;       /* first arrival to last completion */
+} topk_serve_report;
+
+/* Creates a server on `device` with `max_slots` streams (1..64) and a
+ * budget in bytes.  Starts the server's worker thread. */
+topk_status topk_serve_create(topk_server **out, int device, uint64_t hbm_budget,
+                              uint32_t max_slots);
+
+/* Queues a request; *ticket identifies it.  Returns TOPK_EINVAL for bad
+ * arguments and TOPK_EBUDGET when the request alone exceeds the budget
+ * (counted as rejected); nothing is queued then.  Never blocks on the GPU. */
+topk_status topk_serve_submit(topk_server *srv, const topk_request *req, uint64_t *ticket);
+
+/* *done = 1 when the request has finished (its outputs are written). */
+topk_status topk_serve_poll(topk_server *srv, uint64_t ticket, int *done);
+
+/* Waits up to timeout_ns for the request: returns its final status, or
+ * TOPK_ETIMEOUT if it is still running (it keeps running). */
+topk_status topk_serve_wait(topk_server *srv, uint64_t ticket, uint64_t timeout_ns);
+
+/* Counters and latency percentiles of the requests completed so far. */
+topk_status topk_serve_stats(topk_server *srv, topk_serve_report *out);
+
+/* The server's clock (steady, nanoseconds), for topk_request.arrival_ns. */
+uint64_t topk_serve_now_ns(topk_server *srv);
+
+/* Drains every queued and running request, stops the worker, frees the
+ * server. */
+void topk_serve_destroy(topk_server *srv);
+
 /* Synchronises `stream`, then returns and clears the first error latched by
  * device code of this context (TOPK_OK if none). */
 topk_status topk_status_sync(topk_ctx *ctx, void *stream);

@@ -49,6 +49,21 @@ class topk_stats(ctypes.Structure):
                 ("first_candidates", ctypes.c_uint64), ("sample_kept", ctypes.c_uint64)]
 
 
+class topk_request(ctypes.Structure):
+    _fields_ = [("d_keys", ctypes.c_void_p), ("n", ctypes.c_uint64), ("k", ctypes.c_uint64),
+                ("dtype", ctypes.c_int), ("d_out_keys", ctypes.c_void_p), ("d_out_idx", ctypes.c_void_p),
+                ("d_kth_key", ctypes.c_void_p), ("d_kth_idx", ctypes.c_void_p),
+                ("arrival_ns", ctypes.c_uint64)]
+
+
+class topk_serve_report(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("keys", ctypes.c_uint64),
+                ("p50_ns", ctypes.c_uint64), ("p99_ns", ctypes.c_uint64), ("max_ns", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("batched_requests", ctypes.c_uint64),
+                ("peak_inflight_bytes", ctypes.c_uint64), ("elapsed_s", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -79,6 +94,21 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_noalloc"):
         lib.topk_select_noalloc.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, vp, vp]
         lib.topk_select_noalloc.restype = st
+    if hasattr(lib, "topk_serve_create"):
+        lib.topk_serve_create.argtypes = [ctypes.POINTER(vp), i32, u64, u32]
+        lib.topk_serve_create.restype = st
+        lib.topk_serve_submit.argtypes = [vp, ctypes.POINTER(topk_request), ctypes.POINTER(u64)]
+        lib.topk_serve_submit.restype = st
+        lib.topk_serve_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
+        lib.topk_serve_poll.restype = st
+        lib.topk_serve_wait.argtypes = [vp, u64, u64]
+        lib.topk_serve_wait.restype = st
+        lib.topk_serve_stats.argtypes = [vp, ctypes.POINTER(topk_serve_report)]
+        lib.topk_serve_stats.restype = st
+        lib.topk_serve_now_ns.argtypes = [vp]
+        lib.topk_serve_now_ns.restype = u64
+        lib.topk_serve_destroy.argtypes = [vp]
+        lib.topk_serve_destroy.restype = None
     lib.topk_status_sync.argtypes = [vp, vp]
     lib.topk_status_sync.restype = st
     lib.topk_last_stats.argtypes = [vp, ctypes.POINTER(topk_stats)]
@@ -267,6 +297,63 @@ def topk_select_batched(ctx: Context, keys, row_off, row_k, params: topk_params 
     if check:
         _check(ctx.sync(stream), "topk_select_batched (device)")
     return ok, oi, kk, ki, out_off
+
+
+class Server:
+    """topk_serve_*: requests submitted without blocking, admitted under an HBM
+    budget, small ones batched as they arrive, run concurrently on slots."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 64 << 30, max_slots: int = 8):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        _check(lib.topk_serve_create(ctypes.byref(h), int(device), int(hbm_budget), int(max_slots)),
+               "topk_serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def now_ns(self) -> int:
+        return load_library().topk_serve_now_ns(self.handle)
+
+    def submit(self, keys, k: int, out, arrival_ns: int = 0) -> int:
+        """Queues topk_select(keys, k) into ``out`` (the four output tensors of
+        topk_select).  Returns the ticket; raises TopkError on rejection."""
+        ok, oi, kk, ki = out
+        req = topk_request(keys.data_ptr(), keys.numel(), int(k), dtype_code(keys), ok.data_ptr(),
+                           oi.data_ptr(), kk.data_ptr(), ki.data_ptr(), int(arrival_ns))
+        t = ctypes.c_uint64()
+        _check(load_library().topk_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)),
+               "topk_serve_submit")
+        self._keep[t.value] = (keys, out)  # buffers must outlive the request
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        d = ctypes.c_int()
+        _check(load_library().topk_serve_poll(self.handle, int(ticket), ctypes.byref(d)), "topk_serve_poll")
+        return bool(d.value)
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> int:
+        """Final status of the request (TOPK_ETIMEOUT if still running)."""
+        st = load_library().topk_serve_wait(self.handle, int(ticket), int(timeout_s * 1e9))
+        if st != TOPK_ETIMEOUT:
+            self._keep.pop(int(ticket), None)
+        return st
+
+    def stats(self) -> dict:
+        r = topk_serve_report()
+        _check(load_library().topk_serve_stats(self.handle, ctypes.byref(r)), "topk_serve_stats")
+        return {f: getattr(r, f) for f, _ in topk_serve_report._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().topk_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 NOALLOC_MAX_N = 1 << 22

@@ -28,6 +28,16 @@ struct BatchArgs {
     const u64* out_off; // rows + 1
     void* kth_keys;
     u32* kth_idx;
+    // Rows given by pointers instead (used by the serving loop; when set, the
+    // arrays above are ignored): row i has keys row_keys[i][0..row_n[i]),
+    // outputs row_out_keys[i] / row_out_idx[i] (row_k[i] entries) and
+    // row_kth_key[i] / row_kth_idx[i] (one entry).
+    const void* const* row_keys;
+    const u64* row_n;
+    void* const* row_out_keys;
+    u32* const* row_out_idx;
+    void* const* row_kth_key;
+    u32* const* row_kth_idx;
     u32* order;         // rows: row ids, longest first
     u32* queue;         // next index into order
     SelState* states;   // one per block
@@ -45,7 +55,7 @@ __global__ void __launch_bounds__(1024) k_batch_order(BatchArgs b) {
     for (u32 i = threadIdx.x; i < 66; i += blockDim.x) hist[i] = 0;
     __syncthreads();
     for (u32 i = threadIdx.x; i < b.rows; i += blockDim.x) {
-        const u64 len = b.row_off[i + 1] - b.row_off[i];
+        const u64 len = b.row_keys ? b.row_n[i] : b.row_off[i + 1] - b.row_off[i];
         atomicAdd(&hist[len ? 64 - __clzll((long long)len) : 0], 1u);
     }
     __syncthreads();
@@ -59,7 +69,7 @@ __global__ void __launch_bounds__(1024) k_batch_order(BatchArgs b) {
     }
     __syncthreads();
     for (u32 i = threadIdx.x; i < b.rows; i += blockDim.x) {
-        const u64 len = b.row_off[i + 1] - b.row_off[i];
+        const u64 len = b.row_keys ? b.row_n[i] : b.row_off[i + 1] - b.row_off[i];
         const u32 pos = atomicAdd(&start[len ? 64 - __clzll((long long)len) : 0], 1u);
         b.order[pos] = i;
     }
@@ -84,20 +94,30 @@ template <int DT> __global__ void __launch_bounds__(BLK_NT) k_batched(BatchArgs 
         const u32 row = s_row;
         __syncthreads();
         if (row == 0xFFFFFFFFu) break;
-        const u64 r0 = b.row_off[row], n = b.row_off[row + 1] - r0;
+        const bool by_ptr = b.row_keys != nullptr;
+        const u64 r0 = by_ptr ? 0 : b.row_off[row];
+        const u64 n = by_ptr ? b.row_n[row] : b.row_off[row + 1] - r0;
         const u64 k = b.row_k[row];
         if (k == 0 || k > n || n > 0xFFFFFFFFull) {
             if (threadIdx.x == 0) latch(b.err, ST_EINVAL);
             continue;
         }
         SelArgs a{};
-        a.keys = static_cast<const raw_t*>(b.keys) + r0;
+        if (by_ptr) {
+            a.keys = b.row_keys[row];
+            a.out_keys = b.row_out_keys[row];
+            a.out_idx = b.row_out_idx[row];
+            a.kth_key = b.row_kth_key[row];
+            a.kth_idx = b.row_kth_idx[row];
+        } else {
+            a.keys = static_cast<const raw_t*>(b.keys) + r0;
+            a.out_keys = static_cast<raw_t*>(b.out_keys) + b.out_off[row];
+            a.out_idx = b.out_idx + b.out_off[row];
+            a.kth_key = static_cast<raw_t*>(b.kth_keys) + row;
+            a.kth_idx = b.kth_idx + row;
+        }
         a.n = n;
         a.k = k;
-        a.out_keys = static_cast<raw_t*>(b.out_keys) + b.out_off[row];
-        a.out_idx = b.out_idx + b.out_off[row];
-        a.kth_key = static_cast<raw_t*>(b.kth_keys) + row;
-        a.kth_idx = b.kth_idx + row;
         a.cand_key[0] = cand;
         a.cand_key[1] = cand + BATCH_CAP * sizeof(key_t);
         a.cand_idx[0] = reinterpret_cast<u32*>(cand + 2 * BATCH_CAP * sizeof(key_t));
@@ -152,6 +172,38 @@ static topk_status run_batched(topk_ctx* ctx, BatchArgs b, cudaStream_t st) {
     k_batched<DT><<<grid, BLK_NT, sizeof(BlockSmem<KW>), st>>>(b);
     count_launch(ctx, 2);
     return cuda_status(cudaGetLastError());
+}
+
+// Rows given by device pointer arrays (serving).  `ptrs` is one device
+// block laid out as: row_keys[rows], row_out_keys[rows], row_out_idx[rows],
+// row_kth_key[rows], row_kth_idx[rows] (pointers), row_n[rows], row_k[rows].
+topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, u32 rows, const void* ptrs, cudaStream_t st) {
+    const char* p = static_cast<const char*>(ptrs);
+    BatchArgs b{};
+    b.rows = rows;
+    b.row_keys = reinterpret_cast<const void* const*>(p);
+    b.row_out_keys = reinterpret_cast<void* const*>(p + 8ull * rows);
+    b.row_out_idx = reinterpret_cast<u32* const*>(p + 16ull * rows);
+    b.row_kth_key = reinterpret_cast<void* const*>(p + 24ull * rows);
+    b.row_kth_idx = reinterpret_cast<u32* const*>(p + 32ull * rows);
+    b.row_n = reinterpret_cast<const u64*>(p + 40ull * rows);
+    b.row_k = reinterpret_cast<const u32*>(p + 48ull * rows);
+    b.seed = 0xA4093822299F31D0ull;
+    b.parts = 16;
+    b.sample = BATCH_SAMPLE;
+    b.finish_T = dtype == TOPK_U64 ? Lim<64>::ELEMS : Lim<32>::ELEMS;
+    b.z = 4.0f;
+    b.flags = 0;
+    b.err = ctx->d_err;
+    ctx->last_kind = LAST_BATCHED;
+    switch (dtype) {
+    case TOPK_U32: return run_batched<DT_U32>(ctx, b, st);
+    case TOPK_I32: return run_batched<DT_I32>(ctx, b, st);
+    case TOPK_F32: return run_batched<DT_F32>(ctx, b, st);
+    case TOPK_BF16: return run_batched<DT_BF16>(ctx, b, st);
+    case TOPK_U64: return run_batched<DT_U64>(ctx, b, st);
+    default: return TOPK_EINVAL;
+    }
 }
 
 } // namespace topk

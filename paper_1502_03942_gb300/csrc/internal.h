@@ -67,4 +67,9 @@ topk_status cuda_status(cudaError_t e);
 
 int dtype_bytes(topk_dtype dt);
 
+// Batched selection with rows given by device pointer arrays (serving).
+topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, uint32_t rows, const void* ptrs,
+                                cudaStream_t st);
+constexpr uint64_t BATCH_ROW_MAX = 1ull << 18; // longest row the batched kernel takes
+
 } // namespace topk

@@ -1,0 +1,144 @@
+"""topk_serve_*: continuous batching under an HBM budget (GPU).
+
+Every served result must equal the oracle's and the result of the same request
+run alone with topk_select (bit-identical sets, rank-k key and position).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_03942_gb300 import workloads as wl
+
+from _gpu import bits_of, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03942_gb300 as tk
+    return tk
+
+
+def make_request(g, lo, hi):
+    """n log-uniform in [2^lo, 2^hi], u32 or bf16, uniform or Zipf ties,
+    k log-uniform in [1, n/4]."""
+    n = int(2.0 ** g.uniform(lo, hi))
+    name = "u32" if g.integers(0, 2) == 0 else "bf16"
+    zipf = g.integers(0, 2) == 1
+    seed = int(g.integers(0, 1 << 30))
+    if name == "u32":
+        bits = wl.zipf_u32(n, seed) if zipf else wl.uniform_u32(n, seed)
+    else:
+        bits = wl.zipf_bf16_bits(n, seed) if zipf else \
+            np.random.Generator(np.random.Philox(seed)).integers(0, 1 << 16, size=n).astype(np.uint16)
+    k = max(1, min(n, int(2.0 ** g.uniform(0, np.log2(max(2, n / 4))))))
+    return bits, name, k
+
+
+def outputs(torch, keys, k):
+    return (torch.empty(k, dtype=keys.dtype, device="cuda"),
+            torch.empty(k, dtype=torch.uint32, device="cuda"),
+            torch.empty(1, dtype=keys.dtype, device="cuda"),
+            torch.empty(1, dtype=torch.uint32, device="cuda"))
+
+
+def same_result(a, b):
+    ia, ib = bits_of(a[1]), bits_of(b[1])
+    oa, ob = np.argsort(ia), np.argsort(ib)
+    return (np.array_equal(ia[oa], ib[ob]) and np.array_equal(bits_of(a[0])[oa], bits_of(b[0])[ob])
+            and np.array_equal(bits_of(a[2]), bits_of(b[2])) and np.array_equal(bits_of(a[3]), bits_of(b[3])))
+
+
+def test_serve_matches_oracle(tk):
+    """600 small requests submitted in a burst: batched as they arrive."""
+    import torch
+    g = np.random.Generator(np.random.Philox(61))
+    srv = tk.Server(0, hbm_budget=1 << 30, max_slots=4)
+    prepared = []
+    for _ in range(600):
+        bits, name, k = make_request(g, 10, 14)
+        keys = to_device(bits, name)
+        prepared.append((bits, name, k, keys, outputs(torch, keys, k)))
+    torch.cuda.synchronize()
+    # submitted faster than they are served, so waiting requests get batched
+    reqs = [(bits, name, k, out, srv.submit(keys, k, out)) for bits, name, k, keys, out in prepared]
+    for bits, name, k, out, t in reqs:
+        assert srv.wait(t) == tk.TOPK_OK
+        want_sel, want_kth = oracle.select(bits, name, k)
+        assert np.array_equal(np.sort(bits_of(out[1])), np.sort(want_sel))
+        assert int(bits_of(out[3])[0]) == want_kth
+        assert np.array_equal(bits_of(out[0]), bits[bits_of(out[1])])
+    st = srv.stats()
+    assert st["completed"] == 600 and st["failed"] == 0
+    assert st["batched_requests"] == 600 and st["batches"] < 600  # grouped, not one launch each
+    assert st["p50_ns"] > 0 and st["p99_ns"] >= st["p50_ns"]
+    srv.close()
+
+
+def test_serve_alone_vs_mix(tk):
+    """120 requests of mixed sizes (2^10 .. 2^21) served concurrently, then
+    each run alone: the results are bit-identical."""
+    import torch
+    g = np.random.Generator(np.random.Philox(62))
+    srv = tk.Server(0, hbm_budget=8 << 30, max_slots=8)
+    ctx = tk.Context(0)
+    prepared = []
+    for _ in range(120):
+        bits, name, k = make_request(g, 10, 21)
+        keys = to_device(bits, name)
+        prepared.append((keys, k, outputs(torch, keys, k)))
+    torch.cuda.synchronize()
+    reqs = [(keys, k, out, srv.submit(keys, k, out)) for keys, k, out in prepared]
+    for keys, k, out, t in reqs:
+        assert srv.wait(t) == tk.TOPK_OK
+        alone = tk.topk_select(ctx, keys, k)
+        assert same_result(out, alone)
+    st = srv.stats()
+    assert st["completed"] == 120 and st["batches"] >= 1
+    srv.close()
+    ctx.close()
+
+
+def test_serve_budget(tk):
+    import torch
+    keys = to_device(wl.uniform_u32(1 << 20, 63), "u32")
+    out = outputs(torch, keys, 10)
+    need = (1 << 20) * 4 + 10 * 8
+    srv = tk.Server(0, hbm_budget=need // 2, max_slots=2)
+    with pytest.raises(tk.TopkError) as e:
+        srv.submit(keys, 10, out)
+    assert e.value.status == tk.TOPK_EBUDGET
+    assert srv.stats()["rejected"] == 1
+    srv.close()
+    # a budget that fits one request at a time still completes them all
+    srv = tk.Server(0, hbm_budget=need + (1 << 16), max_slots=4)
+    ctx = tk.Context(0)
+    tickets = []
+    outs = [outputs(torch, keys, 10 + i) for i in range(6)]
+    for i in range(6):
+        tickets.append(srv.submit(keys, 10 + i, outs[i]))
+    for i, t in enumerate(tickets):
+        assert srv.wait(t) == tk.TOPK_OK
+        assert same_result(outs[i], tk.topk_select(ctx, keys, 10 + i))
+    st = srv.stats()
+    assert st["peak_inflight_bytes"] <= need + (1 << 16)
+    srv.close()
+    ctx.close()
+
+
+def test_serve_wait_timeout_and_bad_request(tk):
+    import torch
+    keys = to_device(wl.uniform_u32(1 << 24, 64), "u32")
+    srv = tk.Server(0, hbm_budget=1 << 32, max_slots=2)
+    out = outputs(torch, keys, 1000)
+    t = srv.submit(keys, 1000, out)
+    assert srv.wait(t, timeout_s=0.0) in (tk.TOPK_ETIMEOUT, tk.TOPK_OK)
+    assert srv.wait(t) == tk.TOPK_OK
+    assert srv.poll(t)
+    with pytest.raises(tk.TopkError) as e:
+        srv.submit(keys, 0, out)
+    assert e.value.status == tk.TOPK_EINVAL
+    srv.close()

@@ -180,6 +180,161 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------- batched and served extras
+
+def measure_batched(tk, wl, torch, ctx):
+    """4096 rows of N(0,3) f32, lengths 2^U(10,18), k in 1..1024: one
+    graph-captured persistent launch against one topk_select per row."""
+    import numpy as np
+    keys, off, ks = wl.batched_rows(4096, 10, 18, 1024, seed=4)
+    d_keys = torch.from_numpy(keys).cuda()
+    d_off = torch.from_numpy(off.view(np.int64)).cuda().view(torch.uint64)
+    d_k = torch.from_numpy(ks.view(np.int32)).cuda().view(torch.uint32)
+    oo = np.zeros(4097, np.uint64)
+    oo[1:] = np.cumsum(ks.astype(np.uint64))
+    d_oo = torch.from_numpy(oo.view(np.int64)).cuda().view(torch.uint64)
+    total = int(oo[-1])
+    out = (torch.empty(total, dtype=torch.float32, device="cuda"),
+           torch.empty(total, dtype=torch.uint32, device="cuda"),
+           torch.empty(4096, dtype=torch.float32, device="cuda"),
+           torch.empty(4096, dtype=torch.uint32, device="cuda"))
+    for _ in range(3):
+        tk.topk_select_batched(ctx, d_keys, d_off, d_k, out=out, out_off=d_oo, check=False)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        tk.topk_select_batched(ctx, d_keys, d_off, d_k, out=out, out_off=d_oo, check=False)
+    g.replay()
+    torch.cuda.synchronize()
+    reps = 10
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    t_batched = e0.elapsed_time(e1) / reps
+    # one launch sequence per row, same data and outputs
+    rows = [(int(off[i]), int(off[i + 1]), int(ks[i]), int(oo[i])) for i in range(4096)]
+    views = [(d_keys[a:b], k, (out[0][o:o + k], out[1][o:o + k], out[2][i:i + 1], out[3][i:i + 1]))
+             for i, (a, b, k, o) in enumerate(rows)]
+    for v, k, o in views[:64]:
+        tk.topk_select(ctx, v, k, out=o, check=False)
+    torch.cuda.synchronize()
+    e0.record()
+    for v, k, o in views:
+        tk.topk_select(ctx, v, k, out=o, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    t_calls = e0.elapsed_time(e1)
+    st = ctx.sync()
+    n_keys = int(off[-1])
+    return {"workload": "4096 rows f32 N(0,3), n=2^U(10,18), k=U[1,1024], one graph-captured launch",
+            "status": st, "batched_ms": t_batched, "per_call_ms": t_calls,
+            "speedup_vs_per_call": t_calls / t_batched, "keys_per_s": n_keys / (t_batched / 1e3),
+            "algorithmic_GBps": (n_keys * 4 + total * 8) / (t_batched / 1e3) / 1e9}
+
+
+def measure_served(tk, wl, torch, seconds=0.5, rate=20000.0, seed=5):
+    """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
+    uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
+    Inputs come from a pool of distinct device arrays; outputs from a ring
+    arena that is reused only after the request that held it completed."""
+    import collections
+    import numpy as np
+    g = np.random.Generator(np.random.Philox(seed))
+    pool = []
+    for i in range(48):
+        n = int(2.0 ** g.uniform(10, 26))
+        bf16 = bool(g.integers(0, 2))
+        zipf = bool(g.integers(0, 2))
+        if bf16:
+            bits = wl.zipf_bf16_bits(n, 100 + i) if zipf else \
+                np.random.Generator(np.random.Philox(100 + i)).integers(0, 1 << 16, size=n).astype(np.uint16)
+            t = torch.from_numpy(bits.view(np.int16)).cuda().view(torch.bfloat16)
+        else:
+            bits = wl.zipf_u32(n, 100 + i) if zipf else wl.uniform_u32(n, 100 + i)
+            t = torch.from_numpy(bits.view(np.int32)).cuda().view(torch.uint32)
+        pool.append(t)
+    count = int(rate * seconds)
+    gaps = g.exponential(1.0 / rate, size=count)
+    which = g.integers(0, len(pool), size=count)
+    ks = []
+    for i in range(count):
+        n = pool[which[i]].numel()
+        ks.append(max(1, min(n, int(2.0 ** g.uniform(0, np.log2(max(2.0, n / 4)))))))
+    arena_bytes = 6 << 30
+    arena = torch.empty(arena_bytes, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def carve(v, keys, k):
+        """Outputs at virtual arena offset v (monotone; physical = v mod size,
+        never straddling the end).  Returns (outputs, v_start, v_end)."""
+        w = keys.element_size()
+        kbytes = (k * w + 15) & ~15
+        need = kbytes + ((4 * k + 15) & ~15) + 64
+        if v % arena_bytes + need > arena_bytes:
+            v += arena_bytes - v % arena_bytes
+        base = v % arena_bytes
+        kk = arena[base:base + k * w].view(keys.dtype)
+        ii = arena[base + kbytes: base + kbytes + 4 * k].view(torch.uint32)
+        e = (base + kbytes + 4 * k + 15) & ~15
+        kt = arena[e:e + w].view(keys.dtype)
+        it = arena[e + 16:e + 20].view(torch.uint32)
+        return (kk, ii, kt, it), v, v + need
+
+    srv = tk.Server(0, hbm_budget=64 << 30, max_slots=16)
+    inflight = collections.deque()   # (ticket, v_start) in allocation order
+    t0 = srv.now_ns() + 20_000_000
+    when = t0
+    tickets = []
+    v = 0
+    for i in range(count):
+        when += int(gaps[i] * 1e9)
+        keys, k = pool[which[i]], ks[i]
+        out, v0, v1 = carve(v, keys, k)
+        # the physical region is reused: wait for requests allocated more than
+        # one arena length before its end
+        while inflight and inflight[0][1] < v1 - arena_bytes:
+            srv.wait(inflight[0][0])
+            inflight.popleft()
+        v = v1
+        while srv.now_ns() < when:
+            pass
+        t = srv.submit(keys, k, out, arrival_ns=when)
+        tickets.append(t)
+        inflight.append((t, v0))
+    bad = sum(1 for t in tickets if srv.wait(t) != tk.TOPK_OK)
+    st = srv.stats()
+    srv.close()
+    offered_keys = sum(pool[which[i]].numel() for i in range(count))
+    # the same requests, one launch sequence per request, back to back
+    ctx = tk.Context(0)
+    outs = {}
+    for i in range(min(count, 64)):
+        keys, k = pool[which[i]], ks[i]
+        tk.topk_select(ctx, keys, k, out=carve(0, keys, k)[0], check=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(count):
+        keys, k = pool[which[i]], ks[i]
+        tk.topk_select(ctx, keys, k, out=carve(0, keys, k)[0], check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    per_call_s = e0.elapsed_time(e1) / 1e3
+    ctx.close()
+    served_s = st["elapsed_s"]
+    return {"workload": f"Poisson {rate:.0f} req/s for {seconds} s, n=2^U(10,26) u32|bf16 uniform|Zipf, "
+                        "k=2^U(0,log2(n/4)), 64 GB budget, 16 slots",
+            "requests": count, "failed": bad + st["failed"], "p50_ms": st["p50_ns"] / 1e6,
+            "p99_ms": st["p99_ns"] / 1e6, "keys_per_s": st["keys"] / served_s if served_s else None,
+            "offered_keys_per_s": offered_keys / seconds, "batched_requests": st["batched_requests"],
+            "batches": st["batches"], "peak_inflight_GB": st["peak_inflight_bytes"] / 1e9,
+            "per_call_keys_per_s": offered_keys / per_call_s, "per_call_s": per_call_s,
+            "served_s": served_s}
+
+
 # --------------------------------------------------------------- GPU arm
 
 def run_ours(args):
@@ -309,6 +464,13 @@ def run_ours(args):
         "clocks": clocks.summary(),
         "e2e": e2e,
     }
+    if not args.no_extras:
+        for key, fn in (("batched", lambda: measure_batched(tk, wl, torch, ctx)),
+                        ("served", lambda: measure_served(tk, wl, torch))):
+            try:
+                line[key] = fn()
+            except Exception as e:  # reported in the line, never hides the main metric
+                line[key] = {"error": repr(e)}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle()
     print(json.dumps(line), flush=True)
@@ -342,6 +504,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served measurements")
     ap.add_argument("--probe", default=None,
                     help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
     args = ap.parse_args()

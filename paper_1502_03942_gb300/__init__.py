@@ -282,8 +282,8 @@ def topk_select_batched(ctx: Context, keys, row_off, row_k, params: topk_params 
         out_off = torch.zeros(rows + 1, dtype=torch.int64, device=keys.device)
         out_off[1:] = torch.cumsum(row_k.view(torch.int32).to(torch.int64), 0)
         out_off = out_off.view(torch.uint64)
-    total = int(out_off.view(torch.int64)[-1].item())
     if out is None:
+        total = int(out_off.view(torch.int64)[-1].item())
         out = (torch.empty(max(total, 1), dtype=keys.dtype, device=keys.device),
                torch.empty(max(total, 1), dtype=torch.uint32, device=keys.device),
                torch.empty(rows, dtype=keys.dtype, device=keys.device),

@@ -235,6 +235,33 @@ def measure_batched(tk, wl, torch, ctx):
             "algorithmic_GBps": (n_keys * 4 + total * 8) / (t_batched / 1e3) / 1e9}
 
 
+def measure_sorted_runs(tk, wl, torch, ctx):
+    """1024 sorted u64 runs of 2^U(10,20) keys: one multisequence selection
+    per k in {1, 2^16, total/2}."""
+    import numpy as np
+    keys, off = wl.sorted_runs(1024, 10, 20, seed=3)
+    d_keys = torch.from_numpy(keys.view(np.int64)).cuda().view(torch.uint64)
+    d_off = torch.from_numpy(off.view(np.int64)).cuda().view(torch.uint64)
+    total = int(off[-1])
+    res = {"workload": "1024 sorted u64 runs, lengths 2^U(10,20), k in {1, 2^16, total/2}", "total": total}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, k in (("k1", 1), ("k65536", 1 << 16), ("half", total // 2)):
+        out = tk.topk_select_sorted_runs(ctx, d_keys, d_off, k)
+        for _ in range(2):
+            tk.topk_select_sorted_runs(ctx, d_keys, d_off, k, out=out, check=False)
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            tk.topk_select_sorted_runs(ctx, d_keys, d_off, k, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3)}
+    res["status"] = ctx.sync()
+    return res
+
+
 def measure_served(tk, wl, torch, seconds=0.5, rate=20000.0, seed=5):
     """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
     uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
@@ -466,6 +493,7 @@ def run_ours(args):
     }
     if not args.no_extras:
         for key, fn in (("batched", lambda: measure_batched(tk, wl, torch, ctx)),
+                        ("sorted_runs", lambda: measure_sorted_runs(tk, wl, torch, ctx)),
                         ("served", lambda: measure_served(tk, wl, torch))):
             try:
                 line[key] = fn()

@@ -405,15 +405,16 @@ constexpr int TMA_NT = TMA_CONS + 32;
 constexpr u64 WAIT_LIMIT_NS = 200ull * 1000 * 1000;
 
 // Ring geometry.  A sparse pass is memory-bound: a deep ring, 2 blocks per
-// SM.  A dense pass is issue-bound: a shallower ring so that 3 blocks (24
-// consumer warps) fit on an SM.
+// SM.  A dense pass holds two stages per block (one counted, one being
+// written out), so its ring is one or two stages deeper than that, with 3
+// blocks (24 consumer warps) per SM, 2 for 64-bit keys.
 template <int DT, bool DENSE = false> struct TmaCfg {
     static constexpr u32 W = sizeof(typename Key<DT>::raw_t);
     static constexpr u32 TILE = TMA_CONS * 16; // elements per stage
     static constexpr u32 BYTES = TILE * W;     // 8, 16 or 32 KiB
-    static constexpr u32 STAGES = DENSE ? (W == 2 ? 6 : W == 4 ? 3 : 2) : (W == 2 ? 8 : W == 4 ? 5 : 3);
+    static constexpr u32 STAGES = DENSE ? (W == 2 ? 8 : W == 4 ? 4 : 3) : (W == 2 ? 8 : W == 4 ? 5 : 3);
     static constexpr u32 SMEM = STAGES * BYTES;
-    static constexpr int MIN_BLOCKS = DENSE ? 3 : 1;
+    static constexpr int MIN_BLOCKS = DENSE ? (W == 8 ? 2 : 3) : 1;
 };
 
 // MODE: 0 sparse (warp queues), 1 dense, 2 dense with a narrowed window.
@@ -471,26 +472,16 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
     if (MODE == 0 && __any_sync(0xffffffffu, nq)) flush_hits<DT>(wq, nq, sink, lo, pl, pr);
 }
 
-// r[q] for a lane-dependent q without dynamic register indexing (which would
-// move r to local memory): a tree of selects.
-template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) {
-    T l1[8], l2[4], l3[2];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) l1[j] = (q & 1u) ? r[2 * j + 1] : r[2 * j];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) l2[j] = (q & 2u) ? l1[2 * j + 1] : l1[2 * j];
-#pragma unroll
-    for (int j = 0; j < 2; ++j) l3[j] = (q & 4u) ? l2[2 * j + 1] : l2[2 * j];
-    return (q & 8u) ? l3[1] : l3[0];
-}
-
 // Dense levels (most elements in a): output room is reserved per tile with
 // one atomic per class, but the reservation of tile i is issued before the
 // elements of tile i-1 are written, so its latency overlaps real work.  Tile
-// i-1 is re-read from its shared-memory stage (held until then), and its
-// elements are staged per warp in shared memory so that the output is written
-// with fully coalesced stores.  Two threads take turns issuing the atomics so
-// that neither ever waits on its own pending result.
+// i-1 is re-read from its shared-memory stage (held until then).  a-elements
+// leave straight from registers: for each of the 16 slots a warp ballot gives
+// every selected lane its rank, so one store instruction writes the warp's
+// selected elements of that slot to consecutive addresses.  b-elements are
+// few; each lane writes its own at an offset from one warp scan.  Two threads
+// take turns issuing the atomics so that neither waits on its own pending
+// result.
 struct DenseSmem {
     u32 wa[2][TMA_CONS / 32], wb[2][TMA_CONS / 32]; // per-warp counts, by tile parity
     u64 oa[2][TMA_CONS / 32], ob[2][TMA_CONS / 32]; // per-warp offsets inside the tile
@@ -499,8 +490,7 @@ struct DenseSmem {
 
 template <int DT, bool EXACT>
 __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
-                                  uint64_t* empty, u64 my_n, u32* dead, DenseSmem& ds, PassSmem<TMA_CONS>& ps,
-                                  WarpQ<Key<DT>::KW>& st) {
+                                  uint64_t* empty, u64 my_n, u32* dead, DenseSmem& ds, PassSmem<TMA_CONS>& ps) {
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
@@ -512,7 +502,7 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
     constexpr u32 STRIDE = TMA_CONS * EPV; // index distance between a thread's vectors
     const Sink<DT> sink = make_sink<DT>(a, s);
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
-    const u32 warp = threadIdx.x >> 5, lane = lane_id();
+    const u32 warp = threadIdx.x >> 5, lane = lane_id(), below = lanemask_lt();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0
     u32 ma_prev = 0, mb_prev = 0, stg_prev = 0, ib_prev = 0;
     bool ok_prev = false;
@@ -543,12 +533,20 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
                 key_t kk[16];
                 InputSrc<DT>::template load16_smem<TMA_CONS>(
                     reinterpret_cast<const uint4*>(stages + (size_t)stg * Cfg::BYTES), kk);
+                u32 le = 0;
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const ct c = C::make(kk[q], ib + (u32)((q / EPV) * STRIDE + q % EPV));
-                    const bool lt = c < pl;
-                    ma |= (u32)(lt && (!EXACT || c >= lo)) << q;
-                    mb |= (u32)(!lt && c <= pr) << q;
+                    ma |= (u32)(c < pl && (!EXACT || c >= lo)) << q;
+                    le |= (u32)(c <= pr) << q;
+                }
+                mb = le & ~ma;
+                if (EXACT) { // below lo: neither a nor b
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const ct c = C::make(kk[q], ib + (u32)((q / EPV) * STRIDE + q % EPV));
+                        if (c < lo) mb &= ~(1u << q);
+                    }
                 }
             }
             const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
@@ -579,76 +577,59 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
         }
         Sync::sync(); // base of tile i-1 in
         if (have_prev && ok_prev) {
-            uint4 v[NV];
-            const uint4* stage = reinterpret_cast<const uint4*>(stages + (size_t)stg_prev * Cfg::BYTES);
+            // this thread's element of slot q sits at a constant offset from `mine`
+            const unsigned char* mine = stages + (size_t)stg_prev * Cfg::BYTES + threadIdx.x * 16u;
+            auto elem = [&](u32 q) -> raw_t {
+                return *reinterpret_cast<const raw_t*>(mine + (q / EPV) * (TMA_CONS * 16u) + (q % EPV) * sizeof(raw_t));
+            };
+            if (__any_sync(0xffffffffu, ma_prev)) {
+                const u64 xa = ds.ba[ppar] + ds.oa[ppar][warp];
+                if (xa + ds.wa[ppar][warp] <= sink.cap_a) { // the usual case: no per-element bound
+                    raw_t* okp = sink.out_keys + sink.out_base + xa;
+                    u32* oip = sink.out_idx + sink.out_base + xa;
+                    u32 ra = 0;
 #pragma unroll
-            for (int j = 0; j < NV; ++j) v[j] = stage[j * TMA_CONS + threadIdx.x];
+                    for (int q = 0; q < 16; ++q) {
+                        const bool bit = (ma_prev >> q) & 1u;
+                        const u32 bal = __ballot_sync(0xffffffffu, bit);
+                        if (bit) {
+                            const u32 r = ra + (u32)__popc(bal & below);
+                            okp[r] = elem(q);
+                            oip[r] = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
+                        }
+                        ra += (u32)__popc(bal);
+                    }
+                } else {
+                    u64 ra = xa;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const bool bit = (ma_prev >> q) & 1u;
+                        const u32 bal = __ballot_sync(0xffffffffu, bit);
+                        if (bit)
+                            sink.put_a_raw(ra + __popc(bal & below), elem(q),
+                                           ib_prev + (u32)((q / EPV) * STRIDE + q % EPV));
+                        ra += (u32)__popc(bal);
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, mb_prev)) { // b is sparse: each lane writes its own
+                const u32 cnt = (u32)__popc(mb_prev);
+                u32 incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (u32)o) incl += y;
+                }
+                u64 xb = ds.bb[ppar] + ds.ob[ppar][warp] + (incl - cnt);
+                u32 m = mb_prev;
+                while (m) {
+                    const u32 q = (u32)(__ffs(m) - 1);
+                    m &= m - 1;
+                    sink.put_b(xb++, K::fwd(elem(q)), ib_prev + (q / EPV) * STRIDE + q % EPV);
+                }
+            }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[stg_prev]); // keys are in registers: stage may be refilled
-            raw_t rr[16];
-            InputSrc<DT>::unpack_raw(v, rr);
-            // a-elements: every thread appends its own to the warp's staging
-            // area at an offset from one warp scan (both halves packed in one
-            // word), then the warp writes them out with coalesced stores.
-            u64 xa = ds.ba[ppar] + ds.oa[ppar][warp];
-            {
-                const u32 cnt = (u32)__popc(ma_prev & 0xFFu) | ((u32)__popc(ma_prev >> 8) << 16);
-                u32 incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= (u32)o) incl += y;
-                }
-                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
-                const u32 excl = incl - cnt;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const u32 n = h ? (tot >> 16) : (tot & 0xFFFFu);
-                    u32 o = h ? (excl >> 16) : (excl & 0xFFFFu);
-                    const u32 dummy = WarpQ<Key<DT>::KW>::QCAP + lane; // absorbs unselected slots
-#pragma unroll
-                    for (int q = 8 * h; q < 8 * h + 8; ++q) {
-                        const u32 bit = (ma_prev >> q) & 1u;
-                        const u32 d = bit ? o : dummy;
-                        st.k[d] = (key_t)rr[q];
-                        st.i[d] = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
-                        o += bit;
-                    }
-                    __syncwarp();
-                    sink.copy_a(xa, st.k, st.i, n);
-                    __syncwarp();
-                    xa += n;
-                }
-            }
-            if (__any_sync(0xffffffffu, mb_prev)) { // b is sparse: visit set bits only
-                u64 xb = ds.bb[ppar] + ds.ob[ppar][warp];
-                const u32 cnt = (u32)__popc(mb_prev & 0xFFu) | ((u32)__popc(mb_prev >> 8) << 16);
-                u32 incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= (u32)o) incl += y;
-                }
-                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
-                const u32 excl = incl - cnt;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const u32 n = h ? (tot >> 16) : (tot & 0xFFFFu);
-                    u32 o = h ? (excl >> 16) : (excl & 0xFFFFu);
-                    u32 m = (mb_prev >> (8 * h)) & 0xFFu;
-                    while (m) {
-                        const u32 q = (u32)(__ffs(m) - 1) + 8u * h;
-                        m &= m - 1;
-                        st.k[o] = K::fwd(pick16(rr, q));
-                        st.i[o] = ib_prev + (q / EPV) * STRIDE + q % EPV;
-                        ++o;
-                    }
-                    __syncwarp();
-                    sink.copy_b(xb, st.k, st.i, n);
-                    __syncwarp();
-                    xb += n;
-                }
-            }
+            if (lane == 0) mbar_arrive(&empty[stg_prev]); // stage may be refilled
         }
         ma_prev = ma;
         mb_prev = mb;
@@ -677,7 +658,7 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     __shared__ __align__(8) uint64_t full[Cfg::STAGES];
     __shared__ __align__(8) uint64_t empty[Cfg::STAGES];
     __shared__ PassSmem<TMA_CONS> ps;
-    __shared__ WarpQ<KW> wq[TMA_CONS / 32];
+    __shared__ WarpQ<KW> wq[DENSE ? 1 : TMA_CONS / 32];
     __shared__ DenseSmem ds;
     __shared__ u32 dead;
     const SelState s = *a.st;
@@ -720,10 +701,10 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     typedef Comp<KW> C;
     typedef typename C::t ct;
     const ct lo = C::from128(s.lo);
-    WarpQ<KW>& q = wq[threadIdx.x >> 5];
+    WarpQ<KW>& q = wq[DENSE ? 0 : threadIdx.x >> 5];
     if constexpr (!DENSE) tma_consume<DT, 0>(a, s, stages, full, empty, my_n, &dead, ps, q);
-    else if (lo != (ct)0) tma_consume_dense<DT, true>(a, s, stages, full, empty, my_n, &dead, ds, ps, q);
-    else tma_consume_dense<DT, false>(a, s, stages, full, empty, my_n, &dead, ds, ps, q);
+    else if (lo != (ct)0) tma_consume_dense<DT, true>(a, s, stages, full, empty, my_n, &dead, ds, ps);
+    else tma_consume_dense<DT, false>(a, s, stages, full, empty, my_n, &dead, ds, ps);
     SyncNamed<1, TMA_CONS>::sync();
     if (threadIdx.x == 0) pass_epilogue(a);
 }

@@ -256,6 +256,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, u32 parity) {
                  : "memory");
     return ok != 0;
 }
+// As mbar_try_wait, but the thread may stay suspended in the instruction for
+// up to `hint_ns` nanoseconds while the phase is incomplete (it resumes as soon
+// as the phase completes), so a long wait costs few issued instructions.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t* bar, u32 parity, u32 hint_ns) {
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
+                 : "memory");
+    return ok != 0;
+}
 // Waits for phase `parity` of `bar` to complete, for at most ~`limit_ns`
 // nanoseconds of wall time; returns false on timeout.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, u32 parity, u64 limit_ns) {
@@ -263,7 +275,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, u32 parity, u64
     u64 t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_hint(bar, parity, 100000u)) return true;
         u64 t;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         if (t - t0 > limit_ns) return false;

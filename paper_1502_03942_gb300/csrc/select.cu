@@ -431,7 +431,7 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
     const u32 lane = lane_id();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0: input is 16-byte aligned
-    u32 nq = 0;
+    QState qs = QState::make();
     for (u64 i = 0; i < my_n; ++i) {
         const u32 stg = (u32)(i % Cfg::STAGES);
         const u32 parity = (u32)((i / Cfg::STAGES) & 1);
@@ -455,7 +455,7 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
         const u64 tb = (blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE;
         auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
         const u32 valid = ok ? 0xFFFFu : 0u;
-        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, nq);
+        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
         else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
     }
     // the ragged last tile, read directly by the block that owns it
@@ -466,10 +466,10 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
         const u64 tb = nfull * (u64)Cfg::TILE;
         const u32 valid = isrc.template load16<TMA_CONS>(tb, kk, ii);
         auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
-        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, nq);
+        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
         else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
     }
-    if (MODE == 0 && __any_sync(0xffffffffu, nq)) flush_hits<DT>(wq, nq, sink, lo, pl, pr);
+    if (MODE == 0) queue_drain<DT>(wq, qs, sink, lo, pl, pr);
 }
 
 // Dense levels (most elements in a): output room is reserved per tile with
@@ -498,7 +498,7 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
     typedef typename C::t ct;
     typedef TmaCfg<DT, true> Cfg;
     typedef SyncNamed<1, TMA_CONS> Sync;
-    constexpr int EPV = InputSrc<DT>::EPV, NV = InputSrc<DT>::NV;
+    constexpr int EPV = InputSrc<DT>::EPV;
     constexpr u32 STRIDE = TMA_CONS * EPV; // index distance between a thread's vectors
     const Sink<DT> sink = make_sink<DT>(a, s);
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
@@ -592,10 +592,14 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
                     for (int q = 0; q < 16; ++q) {
                         const bool bit = (ma_prev >> q) & 1u;
                         const u32 bal = __ballot_sync(0xffffffffu, bit);
+                        // operands computed on every lane so that the stores
+                        // are predicated rather than branched around
+                        const u32 r = ra + (u32)__popc(bal & below);
+                        const raw_t key = elem(q);
+                        const u32 idx = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
                         if (bit) {
-                            const u32 r = ra + (u32)__popc(bal & below);
-                            okp[r] = elem(q);
-                            oip[r] = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
+                            okp[r] = key;
+                            oip[r] = idx;
                         }
                         ra += (u32)__popc(bal);
                     }

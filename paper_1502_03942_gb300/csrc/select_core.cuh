@@ -444,41 +444,43 @@ __device__ __forceinline__ void classify_emit(const KeyT (&kk)[16], PosF pos, u3
 // When a and b are a small fraction of the source (every k except around
 // n/2), a warp needs no block barrier: one pair comparison per element finds
 // the few elements that can be in a or b (pair <= pr); those are appended to
-// the warp's own shared-memory queue, which is classified exactly and flushed
-// to the output / candidate buffer with one atomic per class per QCAP hits.
+// the warp's own shared-memory queue, which is classified exactly and written
+// to the output / candidate buffer with one atomic per class per full queue.
+//
+// The queue is double-buffered so that a warp never waits for its atomics:
+// when the active queue is full, its classes are counted and the two
+// reservations issued, and the warp goes on filling the other buffer; the
+// full one is written out at the next flush (or at the end of the pass), by
+// which time the reservations have long arrived.  A warp that stopped on
+// every flush would hold its block's shared-memory stage, and with it the
+// whole block, for the atomics' round trip.
 
 template <int KW> struct WarpQ {
-    static constexpr int QCAP = 256;
-    typename Comp<KW>::key_t k[QCAP + 32]; // + one scratch entry per lane for
-    u32 i[QCAP + 32];                      //   branch-free staging
+    static constexpr int QCAP = KW == 32 ? 256 : 192; // fits the 48 KiB static limit at 8 warps
+    typename Comp<KW>::key_t k[2][QCAP];
+    u32 i[2][QCAP];
 };
 
-// Classifies the n queued hits exactly on the pair and writes a-elements to
-// the output and b-elements to the candidate buffer, with one atomic per
-// class (all 32 lanes call).  Kept out of line: it runs rarely, and inlining
-// it into the streaming loop costs instruction-cache space on every tile.
+// Per-warp queue state (uniform across the warp).
+struct QState {
+    u32 nq;     // entries in the active buffer
+    u32 cq;     // active buffer
+    u32 pn;     // entries in the other buffer still to be written (0: none)
+    u64 ra, rb; // lane 0: reservations of those entries (atomics in flight)
+    __device__ static QState make() { return QState{0u, 0u, 0u, 0ull, 0ull}; }
+};
+
+// Writes the n entries of one buffer, whose classes were counted when it was
+// queued, from the reservations ra / rb (lane 0's values).
 template <int DT>
-__device__ __noinline__ void flush_hits(WarpQ<Key<DT>::KW>& q, u32 n, const Sink<DT>& sink,
-                                        typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
-                                        typename Comp<Key<DT>::KW>::t pr) {
+__device__ __forceinline__ void queue_write(const typename Comp<Key<DT>::KW>::key_t* qk, const u32* qi, u32 n,
+                                            u64 ra, u64 rb, const Sink<DT>& sink,
+                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                            typename Comp<Key<DT>::KW>::t pr) {
     typedef Comp<Key<DT>::KW> C;
     typedef typename C::t ct;
-    __syncwarp();
-    u32 ca = 0, cb = 0;
-    for (u32 e = lane_id(); e < n; e += 32) {
-        const ct c = C::make(q.k[e], q.i[e]);
-        if (c >= lo && c < pl) ++ca;
-        else if (c >= pl && c <= pr) ++cb;
-    }
-    ca = __reduce_add_sync(0xffffffffu, ca);
-    cb = __reduce_add_sync(0xffffffffu, cb);
-    u64 ba = 0, bb = 0;
-    if (lane_id() == 0) {
-        if (ca) ba = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ca);
-        if (cb) bb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)cb);
-    }
-    ba = __shfl_sync(0xffffffffu, (unsigned long long)ba, 0);
-    bb = __shfl_sync(0xffffffffu, (unsigned long long)bb, 0);
+    u64 ba = __shfl_sync(0xffffffffu, (unsigned long long)ra, 0);
+    u64 bb = __shfl_sync(0xffffffffu, (unsigned long long)rb, 0);
     const u32 below = lanemask_lt();
     for (u32 e0 = 0; e0 < n; e0 += 32) {
         const u32 e = e0 + lane_id();
@@ -486,8 +488,8 @@ __device__ __noinline__ void flush_hits(WarpQ<Key<DT>::KW>& q, u32 n, const Sink
         typename C::key_t kv = 0;
         u32 iv = 0;
         if (e < n) {
-            kv = q.k[e];
-            iv = q.i[e];
+            kv = qk[e];
+            iv = qi[e];
             const ct c = C::make(kv, iv);
             isa = c >= lo && c < pl;
             isb = c >= pl && c <= pr;
@@ -498,35 +500,82 @@ __device__ __noinline__ void flush_hits(WarpQ<Key<DT>::KW>& q, u32 n, const Sink
         ba += __popc(bala);
         bb += __popc(balb);
     }
+}
+
+// Writes the pending buffer (if any), then counts the classes of the active
+// one, issues its reservations without waiting for them, and switches
+// buffers.  All 32 lanes call.
+template <int DT>
+__device__ __forceinline__ void queue_flush(WarpQ<Key<DT>::KW>& q, QState& qs, const Sink<DT>& sink,
+                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                            typename Comp<Key<DT>::KW>::t pr) {
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename C::t ct;
+    __syncwarp();
+    if (qs.pn) queue_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pn, qs.ra, qs.rb, sink, lo, pl, pr);
+    u32 ca = 0, cb = 0;
+    for (u32 e = lane_id(); e < qs.nq; e += 32) {
+        const ct c = C::make(q.k[qs.cq][e], q.i[qs.cq][e]);
+        ca += (u32)(c >= lo && c < pl);
+        cb += (u32)(c >= pl && c <= pr);
+    }
+    ca = __reduce_add_sync(0xffffffffu, ca);
+    cb = __reduce_add_sync(0xffffffffu, cb);
+    u64 ra = 0, rb = 0;
+    if (lane_id() == 0) {
+        if (ca) ra = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ca);
+        if (cb) rb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)cb);
+    }
+    qs.ra = ra;
+    qs.rb = rb;
+    qs.pn = qs.nq;
+    qs.cq ^= 1u;
+    qs.nq = 0;
+    __syncwarp();
+}
+
+// End of the pass: everything queued is written.
+template <int DT>
+__device__ __forceinline__ void queue_drain(WarpQ<Key<DT>::KW>& q, QState& qs, const Sink<DT>& sink,
+                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                            typename Comp<Key<DT>::KW>::t pr) {
+    if (qs.nq) queue_flush<DT>(q, qs, sink, lo, pl, pr);
+    if (qs.pn) queue_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pn, qs.ra, qs.rb, sink, lo, pl, pr);
+    qs.pn = 0;
     __syncwarp();
 }
 
 // One tile in sparse mode (all 32 lanes call; no block-wide barrier).  Every
 // element with pair <= pr (the only ones that can be in a or b) is queued.
+// The 16 slots go in two halves of at most 8 * 32 <= QCAP hits each, so one
+// flush always makes room; the halves share one copy of the code.
 template <int DT, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
-                                                const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, u32& nq) {
+                                                const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
     typedef Comp<Key<DT>::KW> C;
+    static_assert(8 * 32 <= WarpQ<Key<DT>::KW>::QCAP || Key<DT>::KW == 64, "queue too small");
     u32 hit = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
     hit &= valid;
     if (!__any_sync(0xffffffffu, hit)) return;
     const u32 below = lanemask_lt();
+#pragma unroll 1
+    for (u32 h = 0; h < 2; ++h) {
+        const u32 hh = (hit >> (8 * h)) & 0xFFu;
+        const u32 th = __reduce_add_sync(0xffffffffu, (u32)__popc(hh));
+        if (th == 0) continue;
+        if (qs.nq + th > (u32)WarpQ<Key<DT>::KW>::QCAP) queue_flush<DT>(q, qs, sink, lo, pl, pr);
 #pragma unroll
-    for (int s = 0; s < 16; ++s) {
-        const u32 bal = __ballot_sync(0xffffffffu, (hit >> s) & 1u);
-        if (bal) {
-            if (nq + 32 > (u32)WarpQ<Key<DT>::KW>::QCAP) {
-                flush_hits<DT>(q, nq, sink, lo, pl, pr);
-                nq = 0;
+        for (int s = 0; s < 8; ++s) {
+            const u32 bit = (hh >> s) & 1u;
+            const u32 bal = __ballot_sync(0xffffffffu, bit);
+            if (bit) {
+                const u32 slot = qs.nq + __popc(bal & below);
+                q.k[qs.cq][slot] = h ? kk[8 + s] : kk[s];
+                q.i[qs.cq][slot] = h ? pos(8 + s) : pos(s);
             }
-            if ((hit >> s) & 1u) {
-                const u32 slot = nq + __popc(bal & below);
-                q.k[slot] = kk[s];
-                q.i[slot] = pos(s);
-            }
-            nq += __popc(bal);
+            qs.nq += __popc(bal);
         }
     }
 }
@@ -539,7 +588,7 @@ __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, type
     typedef typename Src::key_t key_t;
     constexpr u64 TILE = (u64)NT * 16;
     const u64 ntiles = (src.extent() + TILE - 1) / TILE;
-    u32 nq = 0;
+    QState qs = QState::make();
     for (u64 t = tile0; t < ntiles; t += tile_step) {
         key_t kk[16];
         u32 ii[16];
@@ -549,9 +598,9 @@ __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, type
             if constexpr (Src::IMPLICIT_IDX) return src.template idx_of<NT>(tb, s);
             else return ii[s];
         };
-        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, q, nq);
+        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, q, qs);
     }
-    if (__any_sync(0xffffffffu, nq)) flush_hits<DT>(q, nq, sink, lo, pl, pr);
+    queue_drain<DT>(q, qs, sink, lo, pl, pr);
 }
 
 // Register path: every thread loads its 16 elements of each tile itself.

@@ -545,10 +545,26 @@ __device__ __forceinline__ void queue_drain(WarpQ<Key<DT>::KW>& q, QState& qs, c
     __syncwarp();
 }
 
+// r[q] for a lane-dependent q without dynamic register indexing (which would
+// move r to local memory): a tree of selects.
+template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) {
+    T l1[8], l2[4], l3[2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) l1[j] = (q & 1u) ? r[2 * j + 1] : r[2 * j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) l2[j] = (q & 2u) ? l1[2 * j + 1] : l1[2 * j];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) l3[j] = (q & 4u) ? l2[2 * j + 1] : l2[2 * j];
+    return (q & 8u) ? l3[1] : l3[0];
+}
+
 // One tile in sparse mode (all 32 lanes call; no block-wide barrier).  Every
 // element with pair <= pr (the only ones that can be in a or b) is queued.
-// The 16 slots go in two halves of at most 8 * 32 <= QCAP hits each, so one
-// flush always makes room; the halves share one copy of the code.
+// Hits are rare, so each lane appends its own at an offset from one warp
+// scan (the counts of both 8-slot halves packed in one word) and visits only
+// its set bits.  The halves hold at most 8 * 32 <= QCAP hits each and go in
+// turn, so one flush always makes room, and they share one copy of the code.
+// pos(q) must accept a lane-dependent q.
 template <int DT, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
                                                 const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
@@ -559,24 +575,30 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
     for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
     hit &= valid;
     if (!__any_sync(0xffffffffu, hit)) return;
-    const u32 below = lanemask_lt();
+    const u32 cnt = (u32)__popc(hit & 0xFFu) | ((u32)__popc(hit >> 8) << 16);
+    u32 incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane_id() >= (u32)o) incl += y;
+    }
+    const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+    const u32 excl = incl - cnt;
 #pragma unroll 1
     for (u32 h = 0; h < 2; ++h) {
-        const u32 hh = (hit >> (8 * h)) & 0xFFu;
-        const u32 th = __reduce_add_sync(0xffffffffu, (u32)__popc(hh));
+        const u32 th = h ? (tot >> 16) : (tot & 0xFFFFu);
         if (th == 0) continue;
         if (qs.nq + th > (u32)WarpQ<Key<DT>::KW>::QCAP) queue_flush<DT>(q, qs, sink, lo, pl, pr);
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const u32 bit = (hh >> s) & 1u;
-            const u32 bal = __ballot_sync(0xffffffffu, bit);
-            if (bit) {
-                const u32 slot = qs.nq + __popc(bal & below);
-                q.k[qs.cq][slot] = h ? kk[8 + s] : kk[s];
-                q.i[qs.cq][slot] = h ? pos(8 + s) : pos(s);
-            }
-            qs.nq += __popc(bal);
+        u32 slot = qs.nq + (h ? (excl >> 16) : (excl & 0xFFFFu));
+        u32 m = (hit >> (8 * h)) & 0xFFu;
+        while (m) {
+            const u32 sq = 8 * h + (u32)(__ffs(m) - 1);
+            m &= m - 1;
+            q.k[qs.cq][slot] = pick16(kk, sq);
+            q.i[qs.cq][slot] = pos((int)sq);
+            ++slot;
         }
+        qs.nq += th;
     }
 }
 
@@ -596,7 +618,7 @@ __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, type
         const u32 valid = src.template load16<NT>(tb, kk, ii);
         auto pos = [&](int s) -> u32 {
             if constexpr (Src::IMPLICIT_IDX) return src.template idx_of<NT>(tb, s);
-            else return ii[s];
+            else return pick16(ii, (u32)s);
         };
         classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, q, qs);
     }

@@ -197,6 +197,14 @@ struct SelArgs {
     u32 samp_cap;
 };
 
+// Largest composite of a key type's domain (the first window's upper end):
+// every composite of that type is at or below it, and the window histogram
+// spreads over the key bits actually used (16 for bf16).
+template <int DT> __host__ __device__ inline u128 key_domain_max() {
+    return DT == DT_U64 ? (((u128)~(u64)0) << 32) | 0xFFFFFFFFu
+                        : (((u128)(DT == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu)) << 32) | 0xFFFFFFFFu;
+}
+
 // Histogram of a window [lo, hi]: bin = (c - lo) >> sh with the shift chosen
 // so that every composite of the window falls in one of HIST_BINS bins.
 constexpr u32 HIST_BITS = 12;

@@ -67,7 +67,7 @@ template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, 
     SelState s;
     if (first) {
         s.lo = 0;
-        s.hi = (u128)C::max_value();
+        s.hi = key_domain_max<DT>();
         s.m_src = a.n;
         s.m_win = a.n;
         s.src = SRC_INPUT;
@@ -86,48 +86,58 @@ template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, 
         ratio = ratio < 1 ? 1 : ratio > SMP_MAX_SCALE ? SMP_MAX_SCALE : ratio;
         draws = (u32)((u64)draws * ratio);
     }
-    const u64 m = s.m_src;
-    const u32 p = (u32)((u64)a.parts < m ? a.parts : m);
-    const u64 len = m / p;
-    const u32 rem = (u32)(m - len * p);
+    if (blockIdx.x * SMP_NT * SMP_DRAWS >= draws) return; // the whole block draws nothing
+    const u32 m = (u32)s.m_src; // sources hold fewer than 2^32 elements
+    const u32 p = a.parts < m ? a.parts : m;
+    const u32 len = m / p, rem = m - len * p;
     const u32 j0 = (blockIdx.x * SMP_NT + threadIdx.x) * SMP_DRAWS;
     const Philox4 r = philox4x32_10(j0, s.level, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
     key_t kk[SMP_DRAWS];
     u32 ii[SMP_DRAWS];
-    bool ok[SMP_DRAWS];
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, m);
     const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
                            a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], m};
+    u32 keepm = 0; // bit q: draw q is inside the window
 #pragma unroll
     for (int q = 0; q < SMP_DRAWS; ++q) {
         const u32 j = j0 + q;
-        ok[q] = j < draws;
         const u32 part = j % p; // draws dealt round-robin: an equal share per partition
-        const u64 plo = (u64)part * len + (part < rem ? part : rem);
-        const u64 psz = len + (part < rem ? 1 : 0);
-        const u64 pos = plo + (((u64)r.v[q] * psz) >> 32);
+        const u32 plo = part * len + (part < rem ? part : rem);
+        const u32 psz = len + (part < rem ? 1 : 0);
+        const u32 pos = plo + (u32)(((u64)r.v[q] * psz) >> 32);
         kk[q] = 0;
         ii[q] = 0;
-        if (ok[q]) {
+        if (j < draws) {
             if (s.src == SRC_INPUT) isrc.at(pos, kk[q], ii[q]);
             else csrc.at(pos, kk[q], ii[q]);
+            const ct c = C::make(kk[q], ii[q]);
+            if (c >= lo && c <= hi) keepm |= 1u << q;
         }
     }
+    // one slot reservation per warp for all its kept draws
+    const u32 cnt = (u32)__popc(keepm);
+    u32 incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane_id() >= (u32)o) incl += y;
+    }
+    const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+    u32 slot0 = 0;
+    if (lane_id() == 31 && tot) slot0 = atomicAdd(a.samp_count, tot);
+    u32 slot = __shfl_sync(0xffffffffu, slot0, 31) + incl - cnt;
     ct* samp = static_cast<ct*>(a.samp);
 #pragma unroll
     for (int q = 0; q < SMP_DRAWS; ++q) {
-        const ct c = C::make(kk[q], ii[q]);
-        const bool keep = ok[q] && c >= lo && c <= hi;
-        const u32 bal = __ballot_sync(0xffffffffu, keep);
-        u32 slot0 = 0;
-        if (lane_id() == 0 && bal) slot0 = atomicAdd(a.samp_count, (u32)__popc(bal));
-        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        const u32 slot = slot0 + __popc(bal & lanemask_lt());
-        if (keep && slot < a.samp_cap) {
-            samp[slot] = c;
-            atomicAdd(&hist[hist_bin(c, lo, sh)], 1u);
-        } else {
-            ok[q] = false;
+        if ((keepm >> q) & 1u) {
+            const ct c = C::make(kk[q], ii[q]);
+            if (slot < a.samp_cap) {
+                samp[slot] = c;
+                atomicAdd(&hist[hist_bin(c, lo, sh)], 1u);
+            } else {
+                keepm &= ~(1u << q);
+            }
+            ++slot;
         }
     }
     __syncthreads();
@@ -135,7 +145,7 @@ template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, 
     // thread to take it)
 #pragma unroll
     for (int q = 0; q < SMP_DRAWS; ++q) {
-        if (!ok[q]) continue;
+        if (!((keepm >> q) & 1u)) continue;
         const u32 b = hist_bin(C::make(kk[q], ii[q]), lo, sh);
         const u32 v = atomicExch(&hist[b], 0u);
         if (v) atomicAdd(a.hist + b, v);
@@ -183,7 +193,7 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
         sm.collect = g->m_win <= a.finish_T;
         const u32 c = *a.samp_count;
         sm.kept = c < a.samp_cap ? c : a.samp_cap;
-        // pivot ranks once (FP64 is slow on this part; the block shares them)
+        // pivot ranks once (the block shares them)
         long long jl = -1, jr = 0;
         if (go && sm.kept > 0)
             pivot_ranks(sm.kept, g->m_win, g->k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
@@ -221,13 +231,15 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
             }
             if (lane == 31) sm.warp_sum[warp] = incl;
             __syncthreads();
-            if (tid == 0) {
-                u32 acc = 0;
-                for (int w = 0; w < PIV_NT / 32; ++w) {
-                    const u32 v = sm.warp_sum[w];
-                    sm.warp_sum[w] = acc;
-                    acc += v;
+            if (warp == 0) { // exclusive scan of the 32 warp totals
+                const u32 v = sm.warp_sum[lane];
+                u32 wi = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 y = __shfl_up_sync(0xffffffffu, wi, o);
+                    if (lane >= (u32)o) wi += y;
                 }
+                sm.warp_sum[lane] = wi - v;
             }
             __syncthreads();
             u32 run = sm.warp_sum[warp] + incl - t;

@@ -43,9 +43,8 @@ __device__ __forceinline__ u32 warp_append(bool keep, u32* counter) {
 }
 
 template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) {
-    typedef Comp<Key<DT>::KW> C;
     g->lo = 0;
-    g->hi = (u128)C::max_value();
+    g->hi = key_domain_max<DT>();
     g->pl = 0;
     g->pr = 0;
     g->m_src = a.n;
@@ -138,7 +137,7 @@ template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>
             kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
         }
         if (kept > 0) {
-            // pivot ranks once (FP64 is slow on this part; the block shares them)
+            // pivot ranks once (the block shares them)
             if (threadIdx.x == 0) {
                 long long l, r;
                 pivot_ranks(kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, l, r);

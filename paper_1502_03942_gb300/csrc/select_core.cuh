@@ -1031,21 +1031,23 @@ __device__ inline void decide(SelState& s) {
 // 0 (the paper's Delta = p^(1/4 + delta) plays this role, Section 2).
 __device__ inline void pivot_ranks(u32 kept, u64 m_win, u64 k_rem, float z, bool raw,
                                    long long& jl, long long& jr) {
-    const double s = (double)kept;
-    const double mu_le = s * (double)k_rem / (double)m_win;
-    const double mu_lt = s * (double)(k_rem - 1) / (double)m_win;
-    const double zz = (double)z;
-    double dle, dlt;
+    // single precision: the ranks only steer the bracket (any pivots give the
+    // exact result), and double precision is slow on this part
+    const float s = (float)kept, m = __ull2float_rn(m_win);
+    const float mu_le = s * (__ull2float_rn(k_rem) / m);
+    const float mu_lt = s * (__ull2float_rn(k_rem - 1) / m);
+    float dle, dlt;
     if (raw) {
-        dle = zz;
-        dlt = zz;
+        dle = z;
+        dlt = z;
     } else {
-        const double vle = mu_le * (1.0 - mu_le / s), vlt = mu_lt * (1.0 - mu_lt / s);
-        dle = zz * sqrt(vle > 0 ? vle : 0) + zz * zz / 3.0 + 1.0;
-        dlt = zz * sqrt(vlt > 0 ? vlt : 0) + zz * zz / 3.0 + 1.0;
+        const float vle = mu_le * (1.0f - mu_le / s), vlt = mu_lt * (1.0f - mu_lt / s);
+        const float extra = z * z / 3.0f + 1.0f;
+        dle = z * sqrtf(fmaxf(vle, 0.0f)) + extra;
+        dlt = z * sqrtf(fmaxf(vlt, 0.0f)) + extra;
     }
-    jl = (long long)floor(mu_le - dle) - 1;
-    jr = (long long)ceil(mu_lt + dlt);
+    jl = (long long)floorf(mu_le - dle) - 1;
+    jr = (long long)ceilf(mu_lt + dlt);
 }
 
 } // namespace topk

@@ -182,21 +182,26 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
     auto& sm = *reinterpret_cast<PivotSmem<KW>*>(smem_raw);
     SelState* g = a.st;
     const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    // the histogram and the state are loaded at once (independent round trips)
+    u32 h[4], t = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = a.hist[tid * 4 + q];
+    const SelState s = first ? initial_state<DT>(a) : *g;
     if (tid == 0) {
-        if (first) init_state<DT>(g, a);
-        u32 go = g->phase == PH_RUN;
-        if (go && g->m_src <= a.grid_G) {
+        if (first) *g = s;
+        u32 go = s.phase == PH_RUN;
+        if (go && s.m_src <= a.grid_G) {
             g->phase = PH_FINISH;
             go = 0;
         }
         sm.flag = go;
-        sm.collect = g->m_win <= a.finish_T;
+        sm.collect = s.m_win <= a.finish_T;
         const u32 c = *a.samp_count;
         sm.kept = c < a.samp_cap ? c : a.samp_cap;
         // pivot ranks once (the block shares them)
         long long jl = -1, jr = 0;
         if (go && sm.kept > 0)
-            pivot_ranks(sm.kept, g->m_win, g->k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+            pivot_ranks(sm.kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
         sm.jl = jl;
         sm.jr = jr;
         for (int q = 0; q < 2; ++q) {
@@ -207,7 +212,6 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
     }
     __syncthreads();
     if (sm.flag) {
-        const SelState s = *g;
         const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
         ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
         const u32 kept = sm.kept;
@@ -217,12 +221,8 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
             const u32 rl = (u32)(jl < 0 ? 0 : jl > top ? top : jl);
             const u32 rr = (u32)(jr < 0 ? 0 : jr > top ? top : jr);
             // exclusive prefix of the histogram (4 bins per thread)
-            u32 h[4], t = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                h[q] = a.hist[tid * 4 + q];
-                t += h[q];
-            }
+            for (int q = 0; q < 4; ++q) t += h[q];
             u32 incl = t;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -270,7 +270,7 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
             const bool same = b0 == b1;
             const u32 off1 = same ? 0 : sm.cnt[0];
             const ct* samp = static_cast<const ct*>(a.samp);
-            constexpr int U = 8; // loads in flight per thread
+            constexpr int U = KW == 32 ? 8 : 4; // loads in flight per thread
             for (u32 base = 0; base < kept; base += PIV_NT * U) {
                 ct cv[U];
 #pragma unroll
@@ -278,15 +278,40 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
                     const u32 i = base + u * PIV_NT + tid;
                     cv[u] = i < kept ? samp[i] : (ct)0;
                 }
+                // one slot reservation per warp and bin for all U elements
+                u32 m0 = 0, m1 = 0;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const u32 i = base + u * PIV_NT + tid;
                     const u32 b = i < kept ? hist_bin(cv[u], lo, sh) : 0xFFFFFFFFu;
-                    const bool in0 = b == b0, in1 = !same && b == b1;
-                    const u32 s0 = warp_append(in0, &sm.want[0]);
-                    const u32 s1 = warp_append(in1, &sm.want[1]);
-                    if (in0 && s0 < sm.cnt[0] && s0 < Lim<KW>::ELEMS) sm.buf[s0] = cv[u];
-                    if (in1 && s1 < sm.cnt[1] && off1 + s1 < Lim<KW>::ELEMS) sm.buf[off1 + s1] = cv[u];
+                    m0 |= (u32)(b == b0) << u;
+                    m1 |= (u32)(!same && b == b1) << u;
+                }
+                const u32 cnt = (u32)__popc(m0) | ((u32)__popc(m1) << 16);
+                u32 incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= (u32)o) incl += y;
+                }
+                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+                u32 w0 = 0, w1 = 0;
+                if (lane == 31) {
+                    if (tot & 0xFFFFu) w0 = atomicAdd(&sm.want[0], tot & 0xFFFFu);
+                    if (tot >> 16) w1 = atomicAdd(&sm.want[1], tot >> 16);
+                }
+                u32 s0 = __shfl_sync(0xffffffffu, w0, 31) + ((incl - cnt) & 0xFFFFu);
+                u32 s1 = __shfl_sync(0xffffffffu, w1, 31) + ((incl - cnt) >> 16);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if ((m0 >> u) & 1u) {
+                        if (s0 < sm.cnt[0] && s0 < Lim<KW>::ELEMS) sm.buf[s0] = cv[u];
+                        ++s0;
+                    }
+                    if ((m1 >> u) & 1u) {
+                        if (s1 < sm.cnt[1] && off1 + s1 < Lim<KW>::ELEMS) sm.buf[off1 + s1] = cv[u];
+                        ++s1;
+                    }
                 }
             }
             __syncthreads();
@@ -737,7 +762,7 @@ template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, 
     }
     __syncthreads();
     if (!sm.flag) return;
-    block_levels_and_finish<DT, true>(a, sm);
+    block_levels_and_finish<DT, true, true>(a, sm);
 }
 
 // k = 1: the minimum pair (base case of Algorithm "select");

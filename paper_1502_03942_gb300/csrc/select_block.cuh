@@ -33,6 +33,21 @@ template <int KW> struct BlockSmem {
 
 __device__ inline void latch(u32* err, u32 code) { atomicCAS(err, 0u, code); }
 
+// All 32 lanes call with their element counts; returns this lane's first
+// slot of a contiguous run reserved for the warp with one atomic.
+__device__ __forceinline__ u32 warp_reserve(u32 cnt, u32* counter) {
+    u32 incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane_id() >= (u32)o) incl += y;
+    }
+    const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
+    u32 base = 0;
+    if (lane_id() == 31 && tot) base = atomicAdd(counter, tot);
+    return __shfl_sync(0xffffffffu, base, 31) + incl - cnt;
+}
+
 // All 32 lanes call; returns the slot of this lane's element when `keep`.
 __device__ __forceinline__ u32 warp_append(bool keep, u32* counter) {
     const u32 bal = __ballot_sync(0xffffffffu, keep);
@@ -42,31 +57,36 @@ __device__ __forceinline__ u32 warp_append(bool keep, u32* counter) {
     return base + __popc(bal & lanemask_lt());
 }
 
-template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) {
-    g->lo = 0;
-    g->hi = key_domain_max<DT>();
-    g->pl = 0;
-    g->pr = 0;
-    g->m_src = a.n;
-    g->m_win = a.n;
-    g->k_rem = a.k;
-    g->out_base = 0;
-    g->cnt_a = 0;
-    g->cnt_b = 0;
-    g->cap_b = a.cap_b;
-    g->first_cand = 0;
-    g->level = 0;
-    g->phase = PH_RUN;
-    g->src = SRC_INPUT;
-    g->dst = SRC_CAND0;
-    g->pending = 0;
-    g->status = ST_OK;
-    g->levels_grid = 0;
-    g->levels_block = 0;
-    g->failures = 0;
-    g->overflows = 0;
-    g->sample_kept = 0;
+// The state of a call before its first level.
+template <int DT> __device__ SelState initial_state(const SelArgs& a) {
+    SelState s;
+    s.lo = 0;
+    s.hi = key_domain_max<DT>();
+    s.pl = 0;
+    s.pr = 0;
+    s.m_src = a.n;
+    s.m_win = a.n;
+    s.k_rem = a.k;
+    s.out_base = 0;
+    s.cnt_a = 0;
+    s.cnt_b = 0;
+    s.cap_b = a.cap_b;
+    s.first_cand = 0;
+    s.level = 0;
+    s.phase = PH_RUN;
+    s.src = SRC_INPUT;
+    s.dst = SRC_CAND0;
+    s.pending = 0;
+    s.status = ST_OK;
+    s.levels_grid = 0;
+    s.levels_block = 0;
+    s.failures = 0;
+    s.overflows = 0;
+    s.sample_kept = 0;
+    s.dense = 0;
+    return s;
 }
+template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) { *g = initial_state<DT>(a); }
 
 // ------------------------------------------------------------ one pass
 
@@ -187,19 +207,30 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src);
     const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
                            a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], s.m_src};
-    for (u64 base = 0; base < s.m_src; base += BLK_NT) {
-        const u64 i = base + threadIdx.x;
-        const bool ok = i < s.m_src;
-        key_t kv = 0;
-        u32 x = 0;
-        if (ok) {
-            if (s.src == SRC_INPUT) isrc.at(i, kv, x);
-            else csrc.at(i, kv, x);
+    constexpr int U = 8; // loads in flight per thread; one slot reservation per warp for all of them
+    for (u64 base = 0; base < s.m_src; base += (u64)BLK_NT * U) {
+        ct cv[U];
+        u32 keepm = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u64 i = base + (u64)u * BLK_NT + threadIdx.x;
+            key_t kv = 0;
+            u32 x = 0;
+            if (i < s.m_src) {
+                if (s.src == SRC_INPUT) isrc.at(i, kv, x);
+                else csrc.at(i, kv, x);
+            }
+            cv[u] = C::make(kv, x);
+            keepm |= (u32)(i < s.m_src && cv[u] >= lo && cv[u] <= hi) << u;
         }
-        const ct c = C::make(kv, x);
-        const bool keep = ok && c >= lo && c <= hi;
-        const u32 slot = warp_append(keep, &sm.kept);
-        if (keep && slot < Lim<KW>::ELEMS) sm.samp[slot] = c;
+        u32 slot = warp_reserve((u32)__popc(keepm), &sm.kept);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if ((keepm >> u) & 1u) {
+                if (slot < Lim<KW>::ELEMS) sm.samp[slot] = cv[u];
+                ++slot;
+            }
+        }
     }
     __syncthreads();
     const u32 count = sm.kept;
@@ -217,15 +248,22 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
     if (threadIdx.x == 0) sm.kept = 0;
     __syncthreads();
     raw_t* ok_out = static_cast<raw_t*>(a.out_keys);
-    for (u32 base = 0; base < count; base += BLK_NT) {
-        const u32 i = base + threadIdx.x;
-        const bool in = i < count;
-        const ct c = in ? sm.samp[i] : (ct)0;
-        const bool sel = in && c <= kth;
-        const u32 slot = warp_append(sel, &sm.kept);
-        if (sel) {
-            ok_out[s.out_base + slot] = K::inv((key_t)C::key(c));
-            a.out_idx[s.out_base + slot] = C::idx(c);
+    for (u32 base = 0; base < count; base += BLK_NT * U) {
+        u32 selm = 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const u32 i = base + u * BLK_NT + threadIdx.x;
+            selm |= (u32)(i < count && sm.samp[i] <= kth) << u;
+        }
+        u32 slot = warp_reserve((u32)__popc(selm), &sm.kept);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if ((selm >> u) & 1u) {
+                const ct c = sm.samp[base + u * BLK_NT + threadIdx.x];
+                ok_out[s.out_base + slot] = K::inv((key_t)C::key(c));
+                a.out_idx[s.out_base + slot] = C::idx(c);
+                ++slot;
+            }
         }
     }
     __syncthreads();
@@ -244,9 +282,32 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
 }
 
 
+// One recursion level run by this block alone: plan, pass, branch.
+template <int DT, bool ONLY_EXACT>
+__device__ __forceinline__ void block_level(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+    SelState* g = a.st;
+    plan_level<DT>(a, sm, false);
+    {
+        const SelState s = *g;
+        run_pass<BLK_NT, DT, false, ONLY_EXACT>(a, s, 0, 1, sm.ps);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) decide(*g);
+    __syncthreads();
+}
+
+// The same, out of line: its register demand then does not weigh on a
+// caller that seldom needs it.
+template <int DT, bool ONLY_EXACT>
+__device__ __noinline__ void block_level_outlined(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+    block_level<DT, ONLY_EXACT>(a, sm);
+}
+
 // Recursion levels run by this block alone until at most T elements remain in
 // the source, then the exact finish.  Precondition: no pass pending.
-template <int DT, bool ONLY_EXACT>
+// OUTLINED keeps the level code out of line (for callers whose source is
+// usually at most T already).
+template <int DT, bool ONLY_EXACT, bool OUTLINED = false>
 __device__ void block_levels_and_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
     SelState* g = a.st;
     for (u32 it = 0; it < MAX_BLOCK_LEVELS; ++it) {
@@ -254,14 +315,8 @@ __device__ void block_levels_and_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>
             block_finish<DT>(a, sm);
             return;
         }
-        plan_level<DT>(a, sm, false);
-        {
-            const SelState s = *g;
-            run_pass<BLK_NT, DT, false, ONLY_EXACT>(a, s, 0, 1, sm.ps);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) decide(*g);
-        __syncthreads();
+        if (OUTLINED) block_level_outlined<DT, ONLY_EXACT>(a, sm);
+        else block_level<DT, ONLY_EXACT>(a, sm);
     }
     if (threadIdx.x == 0) {
         g->status = ST_EINTERNAL;

@@ -72,52 +72,106 @@ def committed_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples while the timed region runs."""
+    """SM clock and clock-event (throttle) reasons sampled while the timed
+    region runs: NVML read directly every 5 ms (read-only queries), else
+    nvidia-smi at its 200 ms minimum period."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-              "clocks_event_reasons.sw_power_cap")
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+    SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                  "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
-        self.rows = []
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.rows = []          # (sm_mhz, max_mhz, reasons set)
+        self.source = None
+        self._stop = threading.Event()
         self.proc = None
+        self.thread = None
+
+    def _nvml_handle(self):
+        import ctypes
+        import torch
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit")
+        pr = torch.cuda.get_device_properties(self.device_index)
+        bus = f"{pr.pci_domain_id:08x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0".encode()
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByPciBusId_v2(ctypes.c_char_p(bus), ctypes.byref(h)) != 0:
+            raise RuntimeError("nvml handle")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        return lib, h, reasons
+
+    def _poll_nvml(self, lib, h, reasons):
+        import ctypes
+        mhz, mx, rs = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 and
+                    reasons(h, ctypes.byref(rs)) == 0):
+                self.rows.append((float(mhz.value), float(mx.value),
+                                  {n for b, n in self.REASONS.items() if rs.value & b}))
+            self._stop.wait(0.005)
+
+    def _read_smi(self):
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.proc.stdout:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) == 7 and p[0].replace(".", "").isdigit() and p[1].replace(".", "").isdigit():
+                self.rows.append((float(p[0]), float(p[1]),
+                                  {names[i] for i in range(4) if p[3 + i].lower() == "active"}))
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
+            lib, h, reasons = self._nvml_handle()
+            self.thread = threading.Thread(target=self._poll_nvml, args=(lib, h, reasons), daemon=True)
+            self.source = "nvml 5 ms"
         except Exception:
-            self.proc = None
+            try:
+                self.proc = subprocess.Popen(
+                    ["nvidia-smi", "-i", str(self.device_index), f"--query-gpu={self.SMI_FIELDS}",
+                     "--format=csv,noheader,nounits", "-lms", "200"],
+                    stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.thread = threading.Thread(target=self._read_smi, daemon=True)
+                self.source = "nvidia-smi 200 ms"
+            except Exception:
+                self.thread = None
+        if self.thread is not None:
+            self.thread.start()
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                self.rows.append(parts)
-
     def __exit__(self, *exc):
+        self._stop.set()
         if self.proc is not None:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows),
+                "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": sorted(set().union(*(r[2] for r in self.rows))),
+                "samples": len(self.rows), "source": self.source}
+
+
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest of every rank's x (a float): the whole job ends when the
+    slowest rank does.  Without a process group, x itself."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def algorithmic_bytes(k):
@@ -181,6 +235,41 @@ def run_reference(args):
 
 
 # ------------------------------------------------- batched and served extras
+
+def measure_plain(tk, wl, torch, ctx):
+    """n = 2^20 u32 uniform keys (seed 1), k = 1000, p = 64: the input is 4 MiB
+    and stays in L2, so the call is timed both warm (back to back) and with
+    L2 flushed before every call (a 256 MiB buffer written in between, outside
+    the call's own events)."""
+    import numpy as np
+    n, k = 1 << 20, 1000
+    x = torch.from_numpy(wl.uniform_u32(n, 1).view(np.int32)).cuda().view(torch.uint32)
+    p = tk.make_params(partitions=64)
+    out = tk.topk_select(ctx, x, k, params=p)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    reps = 50
+    warm, cold = [], []
+    for _ in range(5):
+        tk.topk_select(ctx, x, k, params=p, out=out, check=False)
+    for r in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        tk.topk_select(ctx, x, k, params=p, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        warm.append(e0.elapsed_time(e1))
+        flush.fill_(r & 0xFF)
+        e0.record()
+        tk.topk_select(ctx, x, k, params=p, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        cold.append(e0.elapsed_time(e1))
+    st = ctx.sync()
+    wm, cm = statistics.median(warm), statistics.median(cold)
+    return {"workload": "plain selection: n=2^20 u32 uniform (seed 1), k=1000, p=64", "status": st,
+            "warm_ms": wm, "l2_flushed_ms": cm, "warm_keys_per_s": n / (wm / 1e3),
+            "l2_flushed_keys_per_s": n / (cm / 1e3)}
+
 
 def measure_batched(tk, wl, torch, ctx):
     """4096 rows of N(0,3) f32, lengths 2^U(10,18), k in 1..1024: one
@@ -262,7 +351,7 @@ def measure_sorted_runs(tk, wl, torch, ctx):
     return res
 
 
-def measure_served(tk, wl, torch, seconds=0.5, rate=20000.0, seed=5):
+def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
     uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
     Inputs come from a pool of distinct device arrays; outputs from a ring
@@ -419,10 +508,7 @@ def run_ours(args):
         raise tk.TopkError(st, "timed region")
     prof = ctx.profile_read(reset=True)
     ctx.profile(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
 
     # end to end: pinned host input -> device, select, outputs -> host
     e2e = None
@@ -452,10 +538,7 @@ def run_ours(args):
             e2e_step()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = max_over_ranks(t_e2e, dist, "cuda")
         e2e = {"value": world * steps_e2e * len(DATASETS) * len(KS) * N / t_e2e, "unit": "keys/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
@@ -492,7 +575,8 @@ def run_ours(args):
         "e2e": e2e,
     }
     if not args.no_extras:
-        for key, fn in (("batched", lambda: measure_batched(tk, wl, torch, ctx)),
+        for key, fn in (("plain", lambda: measure_plain(tk, wl, torch, ctx)),
+                        ("batched", lambda: measure_batched(tk, wl, torch, ctx)),
                         ("sorted_runs", lambda: measure_sorted_runs(tk, wl, torch, ctx)),
                         ("served", lambda: measure_served(tk, wl, torch))):
             try:
@@ -532,7 +616,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and served measurements")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain, batched, sorted-runs and served measurements")
     ap.add_argument("--probe", default=None,
                     help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
     args = ap.parse_args()

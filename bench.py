@@ -287,22 +287,28 @@ def measure_batched(tk, wl, torch, ctx):
            torch.empty(total, dtype=torch.uint32, device="cuda"),
            torch.empty(4096, dtype=torch.float32, device="cuda"),
            torch.empty(4096, dtype=torch.uint32, device="cuda"))
-    for _ in range(3):
-        tk.topk_select_batched(ctx, d_keys, d_off, d_k, out=out, out_off=d_oo, check=False)
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g):
-        tk.topk_select_batched(ctx, d_keys, d_off, d_k, out=out, out_off=d_oo, check=False)
-    g.replay()
-    torch.cuda.synchronize()
-    reps = 10
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
+
+    def graph_ms(params):
+        for _ in range(3):
+            tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=params, out=out, out_off=d_oo, check=False)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=params, out=out, out_off=d_oo, check=False)
         g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    t_batched = e0.elapsed_time(e1) / reps
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_default = graph_ms(tk.make_params(block_threads=1024, sample_size=2048))
+    best = tk.topk_tune_batched(ctx, d_keys, d_off, d_k, out, d_oo)
+    t_batched = graph_ms(None)  # the context's tuned choice
     # one launch sequence per row, same data and outputs
     rows = [(int(off[i]), int(off[i + 1]), int(ks[i]), int(oo[i])) for i in range(4096)]
     views = [(d_keys[a:b], k, (out[0][o:o + k], out[1][o:o + k], out[2][i:i + 1], out[3][i:i + 1]))
@@ -320,6 +326,9 @@ def measure_batched(tk, wl, torch, ctx):
     n_keys = int(off[-1])
     return {"workload": "4096 rows f32 N(0,3), n=2^U(10,18), k=U[1,1024], one graph-captured launch",
             "status": st, "batched_ms": t_batched, "per_call_ms": t_calls,
+            "tuned": {"block_threads": best.block_threads, "sample_size": best.sample_size,
+                      "finish_threshold": best.finish_threshold},
+            "untuned_ms": t_default,
             "speedup_vs_per_call": t_calls / t_batched, "keys_per_s": n_keys / (t_batched / 1e3),
             "algorithmic_GBps": (n_keys * 4 + total * 8) / (t_batched / 1e3) / 1e9}
 

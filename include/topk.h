@@ -78,6 +78,11 @@ typedef struct {
                                   finished by one thread block */
     float delta_factor;        /* z: pivot margin in standard deviations */
     uint32_t flags;            /* TOPK_FLAG_* */
+    uint32_t block_threads;    /* topk_select_batched: threads per block
+                                  (256, 512 or 1024); the block's finish
+                                  capacity, and so the largest T, is 16, 8 or
+                                  4 Ki composites of 32-bit keys for 1024,
+                                  512 or 256 threads (half for u64) */
 } topk_params;
 
 /* Counters of the last completed call on a context (valid after
@@ -162,13 +167,46 @@ topk_status topk_select_sorted_runs(topk_ctx *ctx, const void *d_keys,
  *   d_kth_keys, d_kth_idx  rows entries: each row's key and position of
  *              rank k_i.
  * Row lengths must be < 2^32.  Rows with bad k are reported by
- * topk_status_sync() as TOPK_EINVAL (their outputs are left untouched). */
+ * topk_status_sync() as TOPK_EINVAL (their outputs are left untouched).
+ * When params is NULL, or leaves block_threads, sample_size and
+ * finish_threshold all zero, the choice remembered by topk_tune_batched for
+ * this dtype and row count (power-of-two bucket) is used if there is one,
+ * else 1024 threads, a 2048-element sample and the largest T. */
 topk_status topk_select_batched(topk_ctx *ctx, const void *d_keys,
                                 const uint64_t *d_row_off, const uint32_t *d_row_k,
                                 uint32_t rows, topk_dtype dtype, void *d_out_keys,
                                 uint32_t *d_out_idx, const uint64_t *d_out_off,
                                 void *d_kth_keys, uint32_t *d_kth_idx,
                                 const topk_params *params, void *stream);
+
+/* Autotuner of topk_select_batched (no counterpart in the paper): runs the
+ * given batch with every candidate block size (256, 512, 1024 threads),
+ * sample size (1024, 2048, 4096) and finish threshold (the block's capacity
+ * and half of it), times each with CUDA events on `stream` (best of three
+ * after one warm-up), and remembers the fastest for this dtype and row-count
+ * bucket (floor(log2(rows))) in the context.  Arguments as
+ * topk_select_batched; every output is overwritten many times (the last run
+ * uses the chosen setting, so the outputs are that call's result).
+ *   base   NULL or settings copied into every candidate (seed, partitions,
+ *          delta_factor, flags).
+ *   best   NULL or receives the chosen settings.
+ * Blocks the calling thread until the measurements are done.  Returns the
+ * first error of any run (argument errors as topk_select_batched, device
+ * errors as topk_status_sync). */
+topk_status topk_tune_batched(topk_ctx *ctx, const void *d_keys, const uint64_t *d_row_off,
+                              const uint32_t *d_row_k, uint32_t rows, topk_dtype dtype,
+                              void *d_out_keys, uint32_t *d_out_idx, const uint64_t *d_out_off,
+                              void *d_kth_keys, uint32_t *d_kth_idx, const topk_params *base,
+                              topk_params *best, void *stream);
+
+/* The autotuner's remembered choices as a text file: a header line, then one
+ * line per entry: GPU name, dtype, row-count bucket, block_threads,
+ * sample_size, finish_threshold, separated by tabs.  save writes every entry
+ * of the context (TOPK_ECUDA if the file cannot be written); load adds the
+ * entries whose GPU name matches this context's device and returns
+ * TOPK_EINVAL for a missing or malformed file.  Host only; synchronous. */
+topk_status topk_tuning_save(topk_ctx *ctx, const char *path);
+topk_status topk_tuning_load(topk_ctx *ctx, const char *path);
 
 /* Selection without any allocation: the same computation and result as
  * topk_select, for callers that cannot allocate device memory at the point

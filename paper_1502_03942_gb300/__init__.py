@@ -40,7 +40,7 @@ class topk_params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
                 ("sample_size", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
                 ("finish_threshold", ctypes.c_uint32), ("delta_factor", ctypes.c_float),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
 
 
 class topk_stats(ctypes.Structure):
@@ -91,6 +91,13 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_batched"):
         lib.topk_select_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_batched.restype = st
+    if hasattr(lib, "topk_tune_batched"):
+        lib.topk_tune_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.topk_tune_batched.restype = st
+        lib.topk_tuning_save.argtypes = [vp, ctypes.c_char_p]
+        lib.topk_tuning_save.restype = st
+        lib.topk_tuning_load.argtypes = [vp, ctypes.c_char_p]
+        lib.topk_tuning_load.restype = st
     if hasattr(lib, "topk_select_noalloc"):
         lib.topk_select_noalloc.argtypes = [vp, u64, u64, i32, vp, vp, vp, vp, vp, vp]
         lib.topk_select_noalloc.restype = st
@@ -164,8 +171,8 @@ def _ptr(t):
 
 
 def make_params(seed=0, partitions=0, sample_size=0, finish_threshold=0, delta_factor=0.0,
-                flags=0) -> topk_params:
-    return topk_params(seed, partitions, sample_size, 0, finish_threshold, delta_factor, flags)
+                flags=0, block_threads=0) -> topk_params:
+    return topk_params(seed, partitions, sample_size, 0, finish_threshold, delta_factor, flags, block_threads)
 
 
 class Context:
@@ -297,6 +304,30 @@ def topk_select_batched(ctx: Context, keys, row_off, row_k, params: topk_params 
     if check:
         _check(ctx.sync(stream), "topk_select_batched (device)")
     return ok, oi, kk, ki, out_off
+
+
+def topk_tune_batched(ctx: Context, keys, row_off, row_k, out, out_off, base: topk_params | None = None,
+                      stream=None) -> topk_params:
+    """Times every candidate setting of topk_select_batched on this batch and
+    makes the fastest the context's choice for its dtype and row count;
+    returns it.  ``out`` / ``out_off`` as topk_select_batched (overwritten;
+    they end up holding the chosen setting's result)."""
+    ok, oi, kk, ki = out
+    best = topk_params()
+    st = load_library().topk_tune_batched(
+        ctx.handle, _ptr(keys), _ptr(row_off), _ptr(row_k), row_k.numel(), dtype_code(keys), _ptr(ok), _ptr(oi),
+        _ptr(out_off), _ptr(kk), _ptr(ki), ctypes.byref(base) if base is not None else None, ctypes.byref(best),
+        _stream_ptr(stream))
+    _check(st, "topk_tune_batched")
+    return best
+
+
+def topk_tuning_save(ctx: Context, path: str):
+    _check(load_library().topk_tuning_save(ctx.handle, os.fsencode(path)), "topk_tuning_save")
+
+
+def topk_tuning_load(ctx: Context, path: str):
+    _check(load_library().topk_tuning_load(ctx.handle, os.fsencode(path)), "topk_tuning_load")
 
 
 class Server:

@@ -103,6 +103,10 @@ topk_status topk_ctx_create(topk_ctx** out, int device) {
     topk_ctx* c = new topk_ctx();
     c->device = device;
     cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device);
+    {
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->device_name = prop.name;
+    }
     // error word, block-done counters (64 slots), the state and the sample
     // histogram: one allocation, zeroed once; every kernel that uses a
     // counter or the histogram leaves it at zero

@@ -3,6 +3,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
+#include <string>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "../../include/topk.h"
@@ -38,6 +41,9 @@ struct topk_ctx {
     void* d_state = nullptr;       // selection state (SelState or RunsState)
     uint32_t* d_hist = nullptr;    // sample histogram (zero between levels)
     int last_kind = topk::LAST_NONE;
+    std::string device_name;
+    // autotuned batched settings by (dtype, floor(log2(rows)))
+    std::map<std::pair<int, int>, topk_params> tuned;
     topk_stats host_stats{};
     // measurement hooks
     bool profile = false;

@@ -20,12 +20,16 @@ template <int KW> struct Lim {
     static constexpr u32 ELEMS = KW == 32 ? 16384u : 8192u;
 };
 
-template <int KW> struct BlockSmem {
+// Shared memory of a block that runs whole levels: NT threads, room for CAP
+// composites (the sample, then the finisher's candidates; CAP >= T).
+template <int KW, int NT = BLK_NT, u32 CAP = Lim<KW>::ELEMS> struct BlockSmem {
     typedef typename Comp<KW>::t ct;
-    ct samp[Lim<KW>::ELEMS];
+    static constexpr int THREADS = NT;
+    static constexpr u32 ELEMS = CAP;
+    ct samp[CAP];
     RadixSmem<KW, 2> rs2;
     RadixSmem<KW, 1> rs1;
-    PassSmem<BLK_NT> ps;
+    PassSmem<NT> ps;
     u32 kept;
     u32 flag;
     long long jl, jr;
@@ -130,7 +134,7 @@ __device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 ste
 // ------------------------------------------------------- pickPivots
 // Samples the window, reads the pivots off the sample and arms the next pass.
 
-template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm, bool grid_level) {
+template <int DT, class SM> __device__ void plan_level(const SelArgs& a, SM& sm, bool grid_level) {
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
@@ -151,10 +155,10 @@ template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>
         }
         if (s.src == SRC_INPUT) {
             const InputSrc<DT> src = InputSrc<DT>::make(a.keys, s.m_src);
-            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, SM::ELEMS, &sm.kept);
         } else {
             CandSrc<KW> src{static_cast<const key_t*>(a.cand_key[s.src - 1]), a.cand_idx[s.src - 1], s.m_src};
-            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, Lim<KW>::ELEMS, &sm.kept);
+            kept = block_sample(src, lo, hi, draws, a.parts, a.seed, s.level, 0, sm.samp, SM::ELEMS, &sm.kept);
         }
         if (kept > 0) {
             // pivot ranks once (the block shares them)
@@ -192,7 +196,8 @@ template <int DT> __device__ void plan_level(const SelArgs& a, BlockSmem<Key<DT>
 // At most T undecided elements remain in the source: gather them, select the
 // one of rank k_rem, emit every element not above it.
 
-template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+template <int DT, class SM> __device__ void block_finish(const SelArgs& a, SM& sm) {
+    constexpr int NT = SM::THREADS;
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
@@ -208,12 +213,12 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
     const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
                            a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], s.m_src};
     constexpr int U = 8; // loads in flight per thread; one slot reservation per warp for all of them
-    for (u64 base = 0; base < s.m_src; base += (u64)BLK_NT * U) {
+    for (u64 base = 0; base < s.m_src; base += (u64)NT * U) {
         ct cv[U];
         u32 keepm = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const u64 i = base + (u64)u * BLK_NT + threadIdx.x;
+            const u64 i = base + (u64)u * NT + threadIdx.x;
             key_t kv = 0;
             u32 x = 0;
             if (i < s.m_src) {
@@ -227,14 +232,14 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if ((keepm >> u) & 1u) {
-                if (slot < Lim<KW>::ELEMS) sm.samp[slot] = cv[u];
+                if (slot < SM::ELEMS) sm.samp[slot] = cv[u];
                 ++slot;
             }
         }
     }
     __syncthreads();
     const u32 count = sm.kept;
-    if (count != s.m_win || s.k_rem == 0 || s.k_rem > count || count > Lim<KW>::ELEMS) {
+    if (count != s.m_win || s.k_rem == 0 || s.k_rem > count || count > SM::ELEMS) {
         if (threadIdx.x == 0) {
             g->status = ST_EINTERNAL;
             g->phase = PH_ERROR;
@@ -248,18 +253,18 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
     if (threadIdx.x == 0) sm.kept = 0;
     __syncthreads();
     raw_t* ok_out = static_cast<raw_t*>(a.out_keys);
-    for (u32 base = 0; base < count; base += BLK_NT * U) {
+    for (u32 base = 0; base < count; base += NT * U) {
         u32 selm = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const u32 i = base + u * BLK_NT + threadIdx.x;
+            const u32 i = base + u * NT + threadIdx.x;
             selm |= (u32)(i < count && sm.samp[i] <= kth) << u;
         }
         u32 slot = warp_reserve((u32)__popc(selm), &sm.kept);
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if ((selm >> u) & 1u) {
-                const ct c = sm.samp[base + u * BLK_NT + threadIdx.x];
+                const ct c = sm.samp[base + u * NT + threadIdx.x];
                 ok_out[s.out_base + slot] = K::inv((key_t)C::key(c));
                 a.out_idx[s.out_base + slot] = C::idx(c);
                 ++slot;
@@ -283,13 +288,13 @@ template <int DT> __device__ void block_finish(const SelArgs& a, BlockSmem<Key<D
 
 
 // One recursion level run by this block alone: plan, pass, branch.
-template <int DT, bool ONLY_EXACT>
-__device__ __forceinline__ void block_level(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+template <int DT, bool ONLY_EXACT, class SM>
+__device__ __forceinline__ void block_level(const SelArgs& a, SM& sm) {
     SelState* g = a.st;
     plan_level<DT>(a, sm, false);
     {
         const SelState s = *g;
-        run_pass<BLK_NT, DT, false, ONLY_EXACT>(a, s, 0, 1, sm.ps);
+        run_pass<SM::THREADS, DT, false, ONLY_EXACT>(a, s, 0, 1, sm.ps);
     }
     __syncthreads();
     if (threadIdx.x == 0) decide(*g);
@@ -298,8 +303,8 @@ __device__ __forceinline__ void block_level(const SelArgs& a, BlockSmem<Key<DT>:
 
 // The same, out of line: its register demand then does not weigh on a
 // caller that seldom needs it.
-template <int DT, bool ONLY_EXACT>
-__device__ __noinline__ void block_level_outlined(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+template <int DT, bool ONLY_EXACT, class SM>
+__device__ __noinline__ void block_level_outlined(const SelArgs& a, SM& sm) {
     block_level<DT, ONLY_EXACT>(a, sm);
 }
 
@@ -307,8 +312,8 @@ __device__ __noinline__ void block_level_outlined(const SelArgs& a, BlockSmem<Ke
 // the source, then the exact finish.  Precondition: no pass pending.
 // OUTLINED keeps the level code out of line (for callers whose source is
 // usually at most T already).
-template <int DT, bool ONLY_EXACT, bool OUTLINED = false>
-__device__ void block_levels_and_finish(const SelArgs& a, BlockSmem<Key<DT>::KW>& sm) {
+template <int DT, bool ONLY_EXACT, bool OUTLINED = false, class SM>
+__device__ void block_levels_and_finish(const SelArgs& a, SM& sm) {
     SelState* g = a.st;
     for (u32 it = 0; it < MAX_BLOCK_LEVELS; ++it) {
         if (g->m_src <= a.finish_T) {

@@ -59,3 +59,36 @@ def test_binding_fails_loudly_without_library(tmp_path):
             tk.load_library(str(tmp_path / "missing.so"))
     finally:
         tk._lib = saved
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """The binding's ctypes structs have the header's sizes and offsets
+    (a plain C program compiled against include/topk.h prints them)."""
+    import subprocess
+    import paper_1502_03942_gb300 as tk
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "topk.h"\n'
+                   "int main(void) {\n"
+                   '  printf("%zu %zu %zu\\n", sizeof(topk_params), offsetof(topk_params, flags),'
+                   " offsetof(topk_params, block_threads));\n"
+                   '  printf("%zu %zu\\n", sizeof(topk_stats), offsetof(topk_stats, sample_kept));\n'
+                   '  printf("%zu %zu\\n", sizeof(topk_request), offsetof(topk_request, arrival_ns));\n'
+                   '  printf("%zu %zu\\n", sizeof(topk_serve_report), offsetof(topk_serve_report, elapsed_s));\n'
+                   "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [list(map(int, line.split())) for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                                   check=True).stdout.splitlines()]
+    assert got[0] == [ctypes.sizeof(tk.topk_params), tk.topk_params.flags.offset, tk.topk_params.block_threads.offset]
+    assert got[1] == [ctypes.sizeof(tk.topk_stats), tk.topk_stats.sample_kept.offset]
+    assert got[2] == [ctypes.sizeof(tk.topk_request), tk.topk_request.arrival_ns.offset]
+    assert got[3] == [ctypes.sizeof(tk.topk_serve_report), tk.topk_serve_report.elapsed_s.offset]
+
+
+def test_tuning_calls_reject_bad_arguments(lib):
+    lib.topk_tuning_save.restype = ctypes.c_int
+    lib.topk_tuning_load.restype = ctypes.c_int
+    lib.topk_tuning_save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    lib.topk_tuning_load.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    assert lib.topk_tuning_save(None, b"/tmp/x") == 1
+    assert lib.topk_tuning_load(None, b"/tmp/x") == 1

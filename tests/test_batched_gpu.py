@@ -126,3 +126,54 @@ def test_batched_config_full_size(tk, ctx):
     # distinct positions per row
     combo = row_of_out.astype(np.int64) * (1 << 32) + idx
     assert np.unique(combo).size == combo.size
+
+
+@pytest.mark.parametrize("threads", [256, 512, 1024])
+@pytest.mark.parametrize("name", ["f32", "u64"])
+def test_block_variants(tk, ctx, name, threads):
+    """Every block size (and its finish capacity) gives the oracle's rows,
+    including a finish threshold below the capacity and a small sample."""
+    keys, off, ks = rows_for(name, 200, 8, 17, 1024, seed=45)
+    d_keys, d_off, d_k = to_device(keys, name), to_device(off, "u64"), to_device(ks, "u32")
+    for sample, T in ((0, 0), (512, 1024)):
+        p = tk.make_params(block_threads=threads, sample_size=sample, finish_threshold=T)
+        res = tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=p)
+        check_rows(keys, off, ks, name, res, range(200))
+
+
+def test_tuner_choice_and_file(tk, tmp_path):
+    """The tuner's choice is one of the candidates, the outputs it leaves are
+    the oracle's, later calls without settings give the same result, and the
+    choice survives a save / load into a fresh context."""
+    import torch
+    name = "f32"
+    keys, off, ks = rows_for(name, 256, 8, 16, 1024, seed=46)
+    d_keys, d_off, d_k = to_device(keys, name), to_device(off, "u64"), to_device(ks, "u32")
+    c1 = tk.Context(0)
+    ok, oi, kk, ki, out_off = tk.topk_select_batched(c1, d_keys, d_off, d_k)
+    out = (torch.empty_like(ok), torch.empty_like(oi), torch.empty_like(kk), torch.empty_like(ki))
+    best = tk.topk_tune_batched(c1, d_keys, d_off, d_k, out, out_off)
+    assert best.block_threads in (256, 512, 1024)
+    assert best.sample_size in (1024, 2048, 4096) or best.sample_size <= 4096
+    assert best.finish_threshold >= 64
+    check_rows(keys, off, ks, name, (*out, out_off), range(256))
+    again = tk.topk_select_batched(c1, d_keys, d_off, d_k)
+    check_rows(keys, off, ks, name, again, range(0, 256, 7))
+    path = tmp_path / "tuning.txt"
+    tk.topk_tuning_save(c1, str(path))
+    lines = path.read_text().splitlines()
+    assert lines[0] == "topk-tuning 1" and len(lines) == 2
+    fields = lines[1].split("\t")
+    assert fields[3:] == [str(best.block_threads), str(best.sample_size), str(best.finish_threshold)]
+    c2 = tk.Context(0)
+    tk.topk_tuning_load(c2, str(path))
+    path2 = tmp_path / "tuning2.txt"
+    tk.topk_tuning_save(c2, str(path2))
+    assert path2.read_text() == path.read_text()
+    bad = tmp_path / "bad.txt"
+    bad.write_text("not a tuning file\n")
+    with pytest.raises(tk.TopkError) as e:
+        tk.topk_tuning_load(c2, str(bad))
+    assert e.value.status == tk.TOPK_EINVAL
+    c1.close()
+    c2.close()

@@ -266,13 +266,22 @@ topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, u32 rows, const
     b.row_k = reinterpret_cast<const u32*>(p + 48ull * rows);
     b.seed = 0xA4093822299F31D0ull;
     b.parts = 16;
-    b.sample = BATCH_SAMPLE;
-    b.finish_T = dtype == TOPK_U64 ? Lim<64>::ELEMS : Lim<32>::ELEMS;
     b.z = 4.0f;
     b.flags = 0;
     b.err = ctx->d_err;
     ctx->last_kind = LAST_BATCHED;
-    return run_batched_dt(ctx, dtype, b, 1024, st);
+    // the context's tuned setting for this dtype and row count, else the
+    // setting the tuner picks for batches of short rows
+    int threads = 256;
+    b.sample = 1024;
+    b.finish_T = dtype == TOPK_U64 ? Lim<64>::ELEMS : Lim<32>::ELEMS;
+    auto it = ctx->tuned.find({(int)dtype, rows ? 63 - __builtin_clzll((u64)rows) : 0});
+    if (it != ctx->tuned.end()) {
+        threads = (int)it->second.block_threads;
+        b.sample = it->second.sample_size;
+        b.finish_T = it->second.finish_threshold;
+    }
+    return run_batched_dt(ctx, dtype, b, threads, st);
 }
 
 static int log2_floor(u64 v) { return v ? 63 - __builtin_clzll(v) : 0; }

@@ -624,21 +624,24 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
                 if (xa + ds.wa[ppar][warp] <= sink.cap_a) { // the usual case: no per-element bound
                     raw_t* okp = sink.out_keys + sink.out_base + xa;
                     u32* oip = sink.out_idx + sink.out_base + xa;
-                    u32 ra = 0;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
                         const bool bit = (ma_prev >> q) & 1u;
                         const u32 bal = __ballot_sync(0xffffffffu, bit);
                         // operands computed on every lane so that the stores
-                        // are predicated rather than branched around
-                        const u32 r = ra + (u32)__popc(bal & below);
+                        // are predicated rather than branched around; the run
+                        // pointers advance by the slot's count (multiply-add
+                        // unit, leaving the integer unit to the compares)
+                        const u32 r = (u32)__popc(bal & below);
                         const raw_t key = elem(q);
                         const u32 idx = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
                         if (bit) {
                             okp[r] = key;
                             oip[r] = idx;
                         }
-                        ra += (u32)__popc(bal);
+                        const u32 c = (u32)__popc(bal);
+                        okp += c;
+                        oip += c;
                     }
                 } else {
                     u64 ra = xa;

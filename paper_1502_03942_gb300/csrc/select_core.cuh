@@ -422,20 +422,60 @@ __device__ __forceinline__ void classify_emit(const KeyT (&kk)[16], PosF pos, u3
     Sync::sync();
     u64 ra = sm.ba[warp], rb = sm.bb[warp];
     const u32 below = lanemask_lt();
+    typedef typename Key<DT>::raw_t raw_t;
     if (HAS_A && __any_sync(0xffffffffu, ma)) {
+        if (ra + wa <= sink.cap_a) { // the warp's run fits: no per-element bound
+            raw_t* okp = sink.out_keys + sink.out_base + ra;
+            u32* oip = sink.out_idx + sink.out_base + ra;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const u32 bal = __ballot_sync(0xffffffffu, (ma >> s) & 1u);
-            if ((ma >> s) & 1u) sink.put_a(ra + __popc(bal & below), kk[s], pos(s));
-            ra += __popc(bal);
+            for (int s = 0; s < 16; ++s) {
+                const bool bit = (ma >> s) & 1u;
+                const u32 bal = __ballot_sync(0xffffffffu, bit);
+                const u32 r = (u32)__popc(bal & below);
+                const raw_t key = Key<DT>::inv(kk[s]);
+                const u32 x = pos(s);
+                if (bit) {
+                    okp[r] = key;
+                    oip[r] = x;
+                }
+                const u32 c = (u32)__popc(bal);
+                okp += c;
+                oip += c;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const u32 bal = __ballot_sync(0xffffffffu, (ma >> s) & 1u);
+                if ((ma >> s) & 1u) sink.put_a(ra + __popc(bal & below), kk[s], pos(s));
+                ra += __popc(bal);
+            }
         }
     }
     if (__any_sync(0xffffffffu, mb)) {
+        if (rb + wb <= sink.cap_b) {
+            auto* bkp = sink.ck + rb;
+            u32* bip = sink.ci + rb;
 #pragma unroll
-        for (int s = 0; s < 16; ++s) {
-            const u32 bal = __ballot_sync(0xffffffffu, (mb >> s) & 1u);
-            if ((mb >> s) & 1u) sink.put_b(rb + __popc(bal & below), kk[s], pos(s));
-            rb += __popc(bal);
+            for (int s = 0; s < 16; ++s) {
+                const bool bit = (mb >> s) & 1u;
+                const u32 bal = __ballot_sync(0xffffffffu, bit);
+                const u32 r = (u32)__popc(bal & below);
+                const u32 x = pos(s);
+                if (bit) {
+                    bkp[r] = kk[s];
+                    bip[r] = x;
+                }
+                const u32 c = (u32)__popc(bal);
+                bkp += c;
+                bip += c;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 16; ++s) {
+                const u32 bal = __ballot_sync(0xffffffffu, (mb >> s) & 1u);
+                if ((mb >> s) & 1u) sink.put_b(rb + __popc(bal & below), kk[s], pos(s));
+                rb += __popc(bal);
+            }
         }
     }
 }

@@ -324,6 +324,16 @@ topk_status topk_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
                               uint32_t k0, uint32_t k1, uint32_t *d_out,
                               uint32_t count);
 
+/* Diagnostic of the failure path of device waits (no counterpart in the
+ * paper): enqueues on `stream` one block that waits, bounded by limit_us
+ * microseconds (1 .. 10^6), for a pipeline barrier that nothing completes.
+ * The wait expires, TOPK_ETIMEOUT is latched in the context exactly as a
+ * stalled bulk-copy pipeline latches it, and the kernel returns: the next
+ * topk_status_sync() reports TOPK_ETIMEOUT (and clears it), and the context
+ * stays usable.  Returns TOPK_EINVAL for a NULL context or a limit out of
+ * range. */
+topk_status topk_debug_wait_timeout(topk_ctx *ctx, uint32_t limit_us, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

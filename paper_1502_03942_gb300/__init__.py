@@ -91,6 +91,9 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_batched"):
         lib.topk_select_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_batched.restype = st
+    if hasattr(lib, "topk_debug_wait_timeout"):
+        lib.topk_debug_wait_timeout.argtypes = [vp, u32, vp]
+        lib.topk_debug_wait_timeout.restype = st
     if hasattr(lib, "topk_tune_batched"):
         lib.topk_tune_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_tune_batched.restype = st
@@ -320,6 +323,13 @@ def topk_tune_batched(ctx: Context, keys, row_off, row_k, out, out_off, base: to
         _stream_ptr(stream))
     _check(st, "topk_tune_batched")
     return best
+
+
+def topk_debug_wait_timeout(ctx: Context, limit_us: int, stream=None):
+    """Enqueues a bounded wait that expires; topk_status_sync then reports
+    TOPK_ETIMEOUT (see include/topk.h)."""
+    _check(load_library().topk_debug_wait_timeout(ctx.handle, int(limit_us), _stream_ptr(stream)),
+           "topk_debug_wait_timeout")
 
 
 def topk_tuning_save(ctx: Context, path: str):

@@ -84,6 +84,21 @@ __global__ void k_philox(u32 c0, u32 c1, u32 c2, u32 c3, u32 k0, u32 k1, u32* ou
     out[4 * i + 3] = r.v[3];
 }
 
+// A pipeline wait that nothing completes (an mbarrier expecting one arrival
+// that never comes), bounded by limit_ns: the same bounded wait every bulk
+// copy pipeline uses, so this exercises its expiry path, which latches
+// TOPK_ETIMEOUT and returns without a fault.
+__global__ void k_wait_expire(u64 limit_ns, u32* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool done = mbar_wait_bounded(&bar, 0, limit_ns);
+    if (!done && threadIdx.x == 0) atomicCAS(err, 0u, (u32)TOPK_ETIMEOUT);
+}
+
 } // namespace topk
 
 using namespace topk;
@@ -200,6 +215,13 @@ topk_status topk_debug_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3
     k_philox<<<(count + 255) / 256, 256>>>(c0, c1, c2, c3, k0, k1, d_out, count);
     if (cudaGetLastError() != cudaSuccess) return TOPK_ECUDA;
     return cuda_status(cudaDeviceSynchronize());
+}
+
+topk_status topk_debug_wait_timeout(topk_ctx* ctx, uint32_t limit_us, void* stream) {
+    if (!ctx || limit_us == 0 || limit_us > 1000000) return TOPK_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
+    k_wait_expire<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>((u64)limit_us * 1000ull, ctx->d_err);
+    return cuda_status(cudaGetLastError());
 }
 
 } // extern "C"

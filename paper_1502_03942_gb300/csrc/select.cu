@@ -480,18 +480,21 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
         }
         ok = __all_sync(0xffffffffu, ok);
         key_t kk[16];
+        const unsigned char* sb = stages + (size_t)stg * Cfg::BYTES;
         if (ok) {
-            InputSrc<DT>::template load16_smem<TMA_CONS>(
-                reinterpret_cast<const uint4*>(stages + (size_t)stg * Cfg::BYTES), kk);
+            InputSrc<DT>::template load16_smem<TMA_CONS>(reinterpret_cast<const uint4*>(sb), kk);
         } else {
 #pragma unroll
             for (int q = 0; q < 16; ++q) kk[q] = 0;
         }
-        __syncwarp();
-        if (ok && lane == 0) mbar_arrive(&empty[stg]); // stage may be refilled
-        const u64 tb = (blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE;
-        auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
+        // positions in 32 bits (inputs hold fewer than 2^32 keys): slot q of
+        // this thread is ib + (q / EPV) * TMA_CONS * EPV + q % EPV
+        constexpr u32 EPV = InputSrc<DT>::EPV;
+        const u32 ib = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE) + threadIdx.x * EPV;
+        auto pos = [&](int q) -> u32 { return ib + (u32)(q / (int)EPV) * (TMA_CONS * EPV) + (u32)(q % (int)EPV); };
         const u32 valid = ok ? 0xFFFFu : 0u;
+        __syncwarp();
+        if (ok && lane == 0) mbar_arrive(&empty[stg]); // keys are in registers: the stage may be refilled
         if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
         else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
     }

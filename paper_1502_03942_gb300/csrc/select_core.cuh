@@ -608,6 +608,15 @@ template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) 
 template <int DT, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
                                                 const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
+    classify_sparse<DT>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q, qs);
+}
+
+// The same, with key_at(q) giving slot q's key for a lane-dependent q (for
+// instance from a shared-memory stage instead of a tree of selects).
+template <int DT, class CT, class KeyT, class PosF, class KeyAt>
+__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, KeyAt key_at, u32 valid, CT lo,
+                                                CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
+                                                QState& qs) {
     typedef Comp<Key<DT>::KW> C;
     static_assert(8 * 32 <= WarpQ<Key<DT>::KW>::QCAP || Key<DT>::KW == 64, "queue too small");
     u32 hit = 0;
@@ -634,7 +643,7 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
         while (m) {
             const u32 sq = 8 * h + (u32)(__ffs(m) - 1);
             m &= m - 1;
-            q.k[qs.cq][slot] = pick16(kk, sq);
+            q.k[qs.cq][slot] = key_at(sq);
             q.i[qs.cq][slot] = pos((int)sq);
             ++slot;
         }

@@ -601,10 +601,10 @@ template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) 
 // One tile in sparse mode (all 32 lanes call; no block-wide barrier).  Every
 // element with pair <= pr (the only ones that can be in a or b) is queued.
 // Hits are rare, so each lane appends its own at an offset from one warp
-// scan (the counts of both 8-slot halves packed in one word) and visits only
-// its set bits.  The halves hold at most 8 * 32 <= QCAP hits each and go in
-// turn, so one flush always makes room, and they share one copy of the code.
-// pos(q) must accept a lane-dependent q.
+// scan (the per-chunk counts packed in one word) and visits only its set
+// bits.  The 16 slots go in chunks of CH slots, at most CH * 32 <= QCAP hits
+// each, in turn, so one flush always makes room; the chunks share one copy
+// of the code.  pos(q) must accept a lane-dependent q.
 template <int DT, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
                                                 const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
@@ -618,13 +618,20 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
                                                 CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
                                                 QState& qs) {
     typedef Comp<Key<DT>::KW> C;
-    static_assert(8 * 32 <= WarpQ<Key<DT>::KW>::QCAP || Key<DT>::KW == 64, "queue too small");
+    constexpr u32 QCAP = (u32)WarpQ<Key<DT>::KW>::QCAP;
+    constexpr u32 CH = QCAP >= 8 * 32 ? 8 : 4;    // slots per chunk
+    constexpr u32 NCH = 16 / CH;                  // chunks per tile
+    constexpr u32 FB = 32 / NCH;                  // bits per packed chunk count
+    static_assert(CH * 32 <= QCAP, "queue too small for a chunk");
+    static_assert(CH * 32 < (1u << FB), "chunk count does not fit its field");
     u32 hit = 0;
 #pragma unroll
     for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
     hit &= valid;
     if (!__any_sync(0xffffffffu, hit)) return;
-    const u32 cnt = (u32)__popc(hit & 0xFFu) | ((u32)__popc(hit >> 8) << 16);
+    u32 cnt = 0;
+#pragma unroll
+    for (u32 h = 0; h < NCH; ++h) cnt |= (u32)__popc((hit >> (CH * h)) & ((1u << CH) - 1)) << (FB * h);
     u32 incl = cnt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -633,15 +640,16 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
     }
     const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
     const u32 excl = incl - cnt;
+    constexpr u32 FMASK = FB == 32 ? 0xFFFFFFFFu : (1u << FB) - 1;
 #pragma unroll 1
-    for (u32 h = 0; h < 2; ++h) {
-        const u32 th = h ? (tot >> 16) : (tot & 0xFFFFu);
+    for (u32 h = 0; h < NCH; ++h) {
+        const u32 th = (tot >> (FB * h)) & FMASK;
         if (th == 0) continue;
-        if (qs.nq + th > (u32)WarpQ<Key<DT>::KW>::QCAP) queue_flush<DT>(q, qs, sink, lo, pl, pr);
-        u32 slot = qs.nq + (h ? (excl >> 16) : (excl & 0xFFFFu));
-        u32 m = (hit >> (8 * h)) & 0xFFu;
+        if (qs.nq + th > QCAP) queue_flush<DT>(q, qs, sink, lo, pl, pr);
+        u32 slot = qs.nq + ((excl >> (FB * h)) & FMASK);
+        u32 m = (hit >> (CH * h)) & ((1u << CH) - 1);
         while (m) {
-            const u32 sq = 8 * h + (u32)(__ffs(m) - 1);
+            const u32 sq = CH * h + (u32)(__ffs(m) - 1);
             m &= m - 1;
             q.k[qs.cq][slot] = key_at(sq);
             q.i[qs.cq][slot] = pos((int)sq);

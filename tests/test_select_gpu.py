@@ -124,6 +124,29 @@ def test_unaligned_input(tk, ctx, orc, name):
         check_against_oracle(keys[1:], name, k, out, orc)
 
 
+@pytest.mark.parametrize("name", ["u32", "f32", "bf16", "u64"])
+@pytest.mark.parametrize("order", ["ascending", "front", "descending"])
+def test_clustered_hits(tk, ctx, orc, name, order):
+    """Inputs whose selected elements sit together (sorted, or the smallest
+    keys moved to the front): whole tiles are hits of the sparse pass, so its
+    per-warp queues fill in one tile (for 64-bit keys beyond half a tile)."""
+    n = 1 << 20
+    keys = keys_for(name, n, seed=13)
+    by_rank = orc.sort_order(keys, name)
+    if order == "ascending":
+        keys = keys[by_rank]
+    elif order == "descending":
+        keys = keys[by_rank[::-1]]
+    else:
+        small = np.zeros(n, bool)
+        small[by_rank[:40000]] = True
+        keys = np.concatenate([keys[small], keys[~small]])
+    d = to_device(keys, name)
+    for k in (1000, 5000, 30000):
+        out = tk.topk_select(ctx, d, k)
+        check_against_oracle(keys, name, k, out, orc)
+
+
 def test_forced_pivot_failures_stay_exact(tk, ctx, orc):
     n = 1 << 20
     keys = wl.uniform_u32(n, seed=11)

@@ -224,6 +224,18 @@ template <class CT> __device__ __forceinline__ u32 hist_bin(CT c, CT lo, u32 sh)
     return d < (CT)HIST_BINS ? (u32)d : HIST_BINS - 1;
 }
 
+// ------------------------------------------------- dependent launches
+// The kernels of one call are launched with programmatic stream
+// serialization: a kernel's blocks may become resident while the previous
+// kernel is still finishing, and wait here, before their first access to
+// anything the previous kernels wrote, until that grid has completed and its
+// memory is visible.  Each kernel lets its successor start launching at once
+// (its grids are single waves, so the successor's early blocks never keep
+// one of its own blocks from being scheduled).  Without the launch attribute
+// both instructions do nothing.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---------------------------------------------------------- warp helpers
 
 __device__ __forceinline__ u32 lane_id() { return threadIdx.x & 31u; }

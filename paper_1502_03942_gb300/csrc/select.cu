@@ -57,6 +57,8 @@ constexpr int SMP_DRAWS = 4;        // one Philox block per thread
 constexpr u32 SMP_MAX_SCALE = 4;    // extra draws for a narrowed window
 
 template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, int first) {
+    grid_dep_wait();
+    grid_dep_release();
     typedef Key<DT> K;
     typedef typename K::key_t key_t;
     constexpr int KW = K::KW;
@@ -175,6 +177,8 @@ template <int KW> struct PivotSmem {
 constexpr u32 WARP_SELECT_MAX = 4096; // bins up to this size are ranked by one warp
 
 template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, int first) {
+    grid_dep_wait();
+    grid_dep_release();
     constexpr int KW = Key<DT>::KW;
     typedef Comp<KW> C;
     typedef typename C::t ct;
@@ -421,12 +425,16 @@ template <int DT, bool INPUT_ONLY> __device__ void grid_pass(const SelArgs& a, c
 // First level: the source is always the input, so this variant carries no
 // candidate-source code (fewer registers on the pass that reads all n keys).
 template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass_first(SelArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     const SelState s = *a.st;
     if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT) return;
     grid_pass<DT, true>(a, s);
 }
 
 template <int DT> __global__ void __launch_bounds__(PASS_NT) k_pass(SelArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     const SelState s = *a.st;
     if (s.phase != PH_RUN || !s.pending) return;
     grid_pass<DT, false>(a, s);
@@ -708,8 +716,13 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     __shared__ WarpQ<KW> wq[DENSE ? 1 : TMA_CONS / 32];
     __shared__ DenseSmem ds;
     __shared__ u32 dead;
+    grid_dep_wait();
     const SelState s = *a.st;
-    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT || (s.dense != 0) != DENSE) return;
+    if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT || (s.dense != 0) != DENSE) {
+        grid_dep_release(); // the variant not needed lets the next launch proceed at once
+        return;
+    }
+    // the working variant keeps the next kernel's blocks off its SMs until it ends
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < Cfg::STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -758,6 +771,8 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
 
 // Remaining levels in one block, then the exact finish.
 template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, int first) {
+    grid_dep_wait();
+    grid_dep_release();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<BlockSmem<Key<DT>::KW>*>(smem_raw);
     SelState* g = a.st;
@@ -807,6 +822,8 @@ __device__ typename Comp<KW>::t block_extreme(typename Comp<KW>::t v, bool want_
 
 template <int DT>
 __global__ void __launch_bounds__(EXT_NT) k_extreme(SelArgs a, int want_max, u32* counter, void* partials_v) {
+    grid_dep_wait();
+    grid_dep_release();
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     constexpr int KW = K::KW;
@@ -983,6 +1000,23 @@ static u64 candidate_capacity(u64 n, u64 k, const Tuning& tu) {
     return (cap + 4095) & ~(u64)4095;
 }
 
+// Launch with programmatic stream serialization (see grid_dep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Enqueues one selection whose state, error word and buffers `a` already
 // points to.  k = 1 and k = n need `counter` (zero) and `partials`
 // (EXT grid composites).  `ctx` (may be null) receives the measurement hooks.
@@ -993,7 +1027,9 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     const u64 n = a.n, k = a.k;
     if (k == 1 || k == n) {
         if (ctx) profile_pass_begin(ctx, st);
-        k_extreme<DT><<<sms * EXT_BLOCKS_PER_SM, EXT_NT, 0, st>>>(a, k == n && n > 1 ? 1 : 0, counter, partials);
+        const cudaError_t e = launch_dep(k_extreme<DT>, sms * EXT_BLOCKS_PER_SM, EXT_NT, 0, st, a,
+                                         k == n && n > 1 ? 1 : 0, counter, partials);
+        if (e != cudaSuccess) return cuda_status(e);
         if (ctx) {
             profile_pass_end(ctx, st);
             count_launch(ctx);
@@ -1015,19 +1051,23 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     const size_t smem = sizeof(BlockSmem<KW>);
     const int smp_blocks = (int)((tu.sample * SMP_MAX_SCALE + SMP_NT * SMP_DRAWS - 1) / (SMP_NT * SMP_DRAWS));
     for (int l = 0; l < levels; ++l) {
-        k_sample<DT><<<smp_blocks, SMP_NT, 0, st>>>(a, l == 0 ? 1 : 0);
-        k_pivots<DT><<<1, PIV_NT, sizeof(PivotSmem<KW>), st>>>(a, l == 0 ? 1 : 0);
+        cudaError_t e = launch_dep(k_sample<DT>, smp_blocks, SMP_NT, 0, st, a, l == 0 ? 1 : 0);
+        if (e == cudaSuccess) e = launch_dep(k_pivots<DT>, 1, PIV_NT, sizeof(PivotSmem<KW>), st, a, l == 0 ? 1 : 0);
+        if (e != cudaSuccess) return cuda_status(e);
         if (l == 0 && ctx) profile_pass_begin(ctx, st);
         if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY)) {
             // the mode is chosen on the device: the variant that does not match returns at once
-            k_pass_tma<DT, false><<<tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st>>>(a);
-            k_pass_tma<DT, true><<<tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st>>>(a);
+            e = launch_dep(k_pass_tma<DT, false>, tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st, a);
+            if (e == cudaSuccess)
+                e = launch_dep(k_pass_tma<DT, true>, tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st, a);
         }
-        else if (l == 0) k_pass_first<DT><<<pass_grid<DT>(sms, true), PASS_NT, 0, st>>>(a);
-        else k_pass<DT><<<pass_grid<DT>(sms, false), PASS_NT, 0, st>>>(a);
+        else if (l == 0) e = launch_dep(k_pass_first<DT>, pass_grid<DT>(sms, true), PASS_NT, 0, st, a);
+        else e = launch_dep(k_pass<DT>, pass_grid<DT>(sms, false), PASS_NT, 0, st, a);
+        if (e != cudaSuccess) return cuda_status(e);
         if (l == 0 && ctx) profile_pass_end(ctx, st);
     }
-    k_finish<DT><<<1, BLK_NT, smem, st>>>(a, levels == 0 ? 1 : 0);
+    const cudaError_t e = launch_dep(k_finish<DT>, 1, BLK_NT, smem, st, a, levels == 0 ? 1 : 0);
+    if (e != cudaSuccess) return cuda_status(e);
     if (ctx) count_launch(ctx, 3 * (uint64_t)levels + 1 + (levels > 0 && a.aligned ? 1 : 0));
     return cuda_status(cudaGetLastError());
 }

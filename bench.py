@@ -364,8 +364,9 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
     uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
     Inputs come from a pool of distinct device arrays; outputs from a ring
-    arena that is reused only after the request that held it completed."""
-    import collections
+    arena that is reused only after the request that held it completed.  The
+    trace is submitted by the library's native replay at the scheduled times
+    (submit_lag_p99_ms: how late the submissions were)."""
     import numpy as np
     g = np.random.Generator(np.random.Philox(seed))
     pool = []
@@ -408,27 +409,40 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
         it = arena[e + 16:e + 20].view(torch.uint32)
         return (kk, ii, kt, it), v, v + need
 
-    srv = tk.Server(0, hbm_budget=64 << 30, max_slots=16)
-    inflight = collections.deque()   # (ticket, v_start) in allocation order
-    t0 = srv.now_ns() + 20_000_000
-    when = t0
-    tickets = []
+    # the trace: each request's outputs at a virtual arena offset (monotone;
+    # physical = offset mod size, never straddling the end); a request whose
+    # region reuses memory waits (natively, in the replay) for every request
+    # allocated more than one arena length before its end
+    w_of = np.array([pool[which[i]].element_size() for i in range(count)], np.int64)
+    k_arr = np.array(ks, np.int64)
+    kb = (k_arr * w_of + 15) & ~15
+    need = kb + ((4 * k_arr + 15) & ~15) + 64
+    v0 = np.zeros(count, np.int64)
     v = 0
     for i in range(count):
-        when += int(gaps[i] * 1e9)
-        keys, k = pool[which[i]], ks[i]
-        out, v0, v1 = carve(v, keys, k)
-        # the physical region is reused: wait for requests allocated more than
-        # one arena length before its end
-        while inflight and inflight[0][1] < v1 - arena_bytes:
-            srv.wait(inflight[0][0])
-            inflight.popleft()
-        v = v1
-        while srv.now_ns() < when:
-            pass
-        t = srv.submit(keys, k, out, arrival_ns=when)
-        tickets.append(t)
-        inflight.append((t, v0))
+        if v % arena_bytes + need[i] > arena_bytes:
+            v += arena_bytes - v % arena_bytes
+        v0[i] = v
+        v += need[i]
+    v1 = v0 + need
+    done_before = np.searchsorted(v0, v1 - arena_bytes, side="left") - 1
+    phys = v0 % arena_bytes
+    base = arena.data_ptr()
+    reqs = np.zeros(count, dtype=np.dtype(tk.topk_request))
+    reqs["d_keys"] = [pool[which[i]].data_ptr() for i in range(count)]
+    reqs["n"] = [pool[which[i]].numel() for i in range(count)]
+    reqs["k"] = k_arr
+    reqs["dtype"] = [tk.dtype_code(pool[which[i]]) for i in range(count)]
+    reqs["d_out_keys"] = base + phys
+    reqs["d_out_idx"] = base + phys + kb
+    kth = (base + phys + kb + 4 * k_arr + 15) & ~15
+    reqs["d_kth_key"] = kth
+    reqs["d_kth_idx"] = kth + 16
+    srv = tk.Server(0, hbm_budget=64 << 30, max_slots=16)
+    t0 = srv.now_ns() + 20_000_000
+    reqs["arrival_ns"] = t0 + np.cumsum((gaps * 1e9).astype(np.int64))
+    tickets, lags = srv.replay(reqs, done_before)
+    tickets = [int(t) for t in tickets]
     bad = sum(1 for t in tickets if srv.wait(t) != tk.TOPK_OK)
     st = srv.stats()
     srv.close()
@@ -457,7 +471,8 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
             "offered_keys_per_s": offered_keys / seconds, "batched_requests": st["batched_requests"],
             "batches": st["batches"], "peak_inflight_GB": st["peak_inflight_bytes"] / 1e9,
             "per_call_keys_per_s": offered_keys / per_call_s, "per_call_s": per_call_s,
-            "served_s": served_s}
+            "served_s": served_s,
+            "submit_lag_p99_ms": float(np.percentile(lags, 99)) / 1e6}
 
 
 # --------------------------------------------------------------- GPU arm

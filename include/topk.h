@@ -270,7 +270,11 @@ typedef struct {
 } topk_serve_report;
 
 /* Creates a server on `device` with `max_slots` streams (1..64) and a
- * budget in bytes.  Starts the server's worker thread. */
+ * budget in bytes.  Starts the server's worker thread.  Every slot owns a
+ * context whose scratch is reserved up front for a selection of 2^26 64-bit
+ * keys and a batch of 2048 rows (about 0.6 GiB per slot, outside the
+ * budget), so that serving seldom allocates; larger requests grow it on first
+ * use.  TOPK_ENOMEM if that memory is not available. */
 topk_status topk_serve_create(topk_server **out, int device, uint64_t hbm_budget,
                               uint32_t max_slots);
 
@@ -288,6 +292,20 @@ topk_status topk_serve_wait(topk_server *srv, uint64_t ticket, uint64_t timeout_
 
 /* Counters and latency percentiles of the requests completed so far. */
 topk_status topk_serve_stats(topk_server *srv, topk_serve_report *out);
+
+/* Open-loop replay of a request trace (a load generator; no counterpart in
+ * the paper): submits reqs[i] when topk_serve_now_ns() reaches
+ * reqs[i].arrival_ns (at once when that is 0 or past), in order, from the
+ * calling thread.  done_before[i] (< i, or -1 for none) names the earliest
+ * earlier requests whose outputs reqs[i] reuses: the call first waits until
+ * every request with index <= done_before[i] has finished.  tickets[i]
+ * receives the ticket (0 when the request was rejected); lag_ns (NULL or
+ * count entries) how late each submission was against its schedule.  All
+ * arrays are host memory.  Returns when the last request is submitted (not
+ * finished); TOPK_ETIMEOUT if a wait exceeded 60 s, TOPK_EINVAL for bad
+ * arguments (done_before[i] >= i included). */
+topk_status topk_serve_replay(topk_server *srv, const topk_request *reqs, const int64_t *done_before,
+                              uint64_t count, uint64_t *tickets, uint64_t *lag_ns);
 
 /* The server's clock (steady, nanoseconds), for topk_request.arrival_ns. */
 uint64_t topk_serve_now_ns(topk_server *srv);

@@ -108,6 +108,9 @@ def load_library(path: str = LIB_PATH):
         lib.topk_serve_create.argtypes = [ctypes.POINTER(vp), i32, u64, u32]
         lib.topk_serve_create.restype = st
         lib.topk_serve_submit.argtypes = [vp, ctypes.POINTER(topk_request), ctypes.POINTER(u64)]
+        if hasattr(lib, "topk_serve_replay"):
+            lib.topk_serve_replay.argtypes = [vp, vp, vp, u64, vp, vp]
+            lib.topk_serve_replay.restype = st
         lib.topk_serve_submit.restype = st
         lib.topk_serve_poll.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int)]
         lib.topk_serve_poll.restype = st
@@ -378,6 +381,23 @@ class Server:
         if st != TOPK_ETIMEOUT:
             self._keep.pop(int(ticket), None)
         return st
+
+    def replay(self, reqs, done_before, want_lags: bool = True):
+        """topk_serve_replay over a numpy array of topk_request records
+        (dtype ``np.dtype(topk_request)``) and an int64 array ``done_before``.
+        The caller keeps every input and output buffer alive until the
+        requests finish.  Returns (tickets, lags_ns) as numpy uint64 arrays."""
+        import numpy as np
+        count = len(reqs)
+        reqs = np.ascontiguousarray(reqs)
+        done_before = np.ascontiguousarray(done_before, dtype=np.int64)
+        tickets = np.zeros(count, np.uint64)
+        lags = np.zeros(count, np.uint64) if want_lags else None
+        _check(load_library().topk_serve_replay(
+            self.handle, reqs.ctypes.data_as(ctypes.c_void_p), done_before.ctypes.data_as(ctypes.c_void_p),
+            count, tickets.ctypes.data_as(ctypes.c_void_p),
+            lags.ctypes.data_as(ctypes.c_void_p) if lags is not None else None), "topk_serve_replay")
+        return tickets, lags
 
     def stats(self) -> dict:
         r = topk_serve_report()

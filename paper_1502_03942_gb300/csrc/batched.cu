@@ -73,6 +73,8 @@ struct BatchArgs {
 
 // Orders the rows by floor(log2(length)), longest first (one block).
 __global__ void __launch_bounds__(1024) k_batch_order(BatchArgs b) {
+    grid_dep_wait();
+    grid_dep_release();
     __shared__ u32 hist[66], start[66];
     for (u32 i = threadIdx.x; i < 66; i += blockDim.x) hist[i] = 0;
     __syncthreads();
@@ -99,6 +101,7 @@ __global__ void __launch_bounds__(1024) k_batch_order(BatchArgs b) {
 
 template <int DT, int NT>
 __global__ void __launch_bounds__(NT, (BatchVariant<Key<DT>::KW, NT>::MINB)) k_batched(BatchArgs b) {
+    grid_dep_wait();
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
@@ -194,8 +197,9 @@ static topk_status launch_batched(topk_ctx* ctx, const BatchArgs& b, cudaStream_
     topk_status rs;
     const int per_sm = batched_blocks_per_sm<DT, NT>(ctx->device, rs);
     if (rs != TOPK_OK) return rs;
-    k_batch_order<<<1, 1024, 0, st>>>(b);
-    k_batched<DT, NT><<<ctx->sms * per_sm, NT, sizeof(BatchSmem<KW, NT>), st>>>(b);
+    cudaError_t e = launch_dep(k_batch_order, 1, 1024, 0, st, b);
+    if (e == cudaSuccess) e = launch_dep(k_batched<DT, NT>, ctx->sms * per_sm, NT, sizeof(BatchSmem<KW, NT>), st, b);
+    if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx, 2);
     return cuda_status(cudaGetLastError());
 }
@@ -210,6 +214,20 @@ template <int DT> static int batched_max_grid(topk_ctx* ctx, topk_status& rs) {
     return ctx->sms * m;
 }
 
+// Scratch regions of one batched launch over `rows` rows with `grid` blocks.
+struct BatchCarve {
+    size_t order, queue, states, cand;
+};
+template <int DT> static Carve batch_carve(u32 rows, int grid, BatchCarve& bc) {
+    typedef typename Key<DT>::key_t key_t;
+    Carve cv;
+    bc.order = cv.take(4ull * rows);
+    bc.queue = cv.take(256);
+    bc.states = cv.take(sizeof(SelState) * (size_t)grid);
+    bc.cand = cv.take((size_t)grid * 2 * BATCH_CAP * (sizeof(key_t) + 4));
+    return cv;
+}
+
 template <int DT>
 static topk_status run_batched(topk_ctx* ctx, BatchArgs b, int threads, cudaStream_t st) {
     typedef typename Key<DT>::key_t key_t;
@@ -221,11 +239,9 @@ static topk_status run_batched(topk_ctx* ctx, BatchArgs b, int threads, cudaStre
                                    : threads == 512 ? BatchVariant<KW, 512>::CAP : BatchVariant<KW, 1024>::CAP;
     b.finish_T = std::min(b.finish_T, cap);
     b.sample = std::min(b.sample, cap);
-    Carve cv;
-    const size_t o_order = cv.take(4ull * b.rows);
-    const size_t o_queue = cv.take(256);
-    const size_t o_states = cv.take(sizeof(SelState) * (size_t)grid);
-    const size_t o_cand = cv.take((size_t)grid * 2 * BATCH_CAP * (sizeof(key_t) + 4));
+    BatchCarve bc;
+    const Carve cv = batch_carve<DT>(b.rows, grid, bc);
+    const size_t o_order = bc.order, o_queue = bc.queue, o_states = bc.states, o_cand = bc.cand;
     rs = ensure_scratch(ctx, cv.off);
     if (rs != TOPK_OK) return rs;
     char* base = static_cast<char*>(ctx->scratch.base);
@@ -285,6 +301,26 @@ topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, u32 rows, const
 }
 
 static int log2_floor(u64 v) { return v ? 63 - __builtin_clzll(v) : 0; }
+
+template <int DT> static topk_status batched_reserve_dt(topk_ctx* ctx, uint32_t rows) {
+    topk_status rs = TOPK_OK;
+    const int grid = batched_max_grid<DT>(ctx, rs);
+    if (rs != TOPK_OK) return rs;
+    BatchCarve bc;
+    return ensure_scratch(ctx, batch_carve<DT>(rows, grid, bc).off);
+}
+
+topk_status batched_reserve(topk_ctx* ctx, topk_dtype dtype, uint32_t rows) {
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
+    switch (dtype) {
+    case TOPK_U32: return batched_reserve_dt<DT_U32>(ctx, rows);
+    case TOPK_I32: return batched_reserve_dt<DT_I32>(ctx, rows);
+    case TOPK_F32: return batched_reserve_dt<DT_F32>(ctx, rows);
+    case TOPK_BF16: return batched_reserve_dt<DT_BF16>(ctx, rows);
+    case TOPK_U64: return batched_reserve_dt<DT_U64>(ctx, rows);
+    default: return TOPK_EINVAL;
+    }
+}
 
 // Arguments of one topk_select_batched call (after validation) with the
 // settings of `p`; `threads` receives the block size.

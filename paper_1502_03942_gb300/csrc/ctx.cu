@@ -183,14 +183,16 @@ void topk_ctx_destroy(topk_ctx* ctx) {
 topk_status topk_status_sync(topk_ctx* ctx, void* stream) {
     if (!ctx) return TOPK_EINVAL;
     cudaSetDevice(ctx->device);
-    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return TOPK_ECUDA;
+    // the error word is read on the caller's stream (a plain cudaMemcpy would
+    // go through the legacy default stream and wait for unrelated work)
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
     u32 err = 0;
-    if (cudaMemcpy(&err, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpyAsync(&err, ctx->d_err, sizeof(u32), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return TOPK_ECUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return TOPK_ECUDA;
     if (err != 0) {
-        if (cudaMemset(ctx->d_err, 0, sizeof(u32)) != cudaSuccess) return TOPK_ECUDA;
-        cudaDeviceSynchronize();
+        if (cudaMemsetAsync(ctx->d_err, 0, sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return TOPK_ECUDA;
     }
     return static_cast<topk_status>(err);
 }

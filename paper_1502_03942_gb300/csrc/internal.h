@@ -73,9 +73,31 @@ topk_status cuda_status(cudaError_t e);
 
 int dtype_bytes(topk_dtype dt);
 
+// Kernel launch with programmatic stream serialization: the kernel's blocks
+// may become resident before the previous kernel on the stream has ended;
+// every kernel launched this way waits for its predecessor's grid on the
+// device (grid_dep_wait in common.cuh) before touching its results.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Batched selection with rows given by device pointer arrays (serving).
 topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, uint32_t rows, const void* ptrs,
                                 cudaStream_t st);
 constexpr uint64_t BATCH_ROW_MAX = 1ull << 18; // longest row the batched kernel takes
+// Grows the context's scratch for a batched launch of up to `rows` rows.
+topk_status batched_reserve(topk_ctx* ctx, topk_dtype dtype, uint32_t rows);
 
 } // namespace topk

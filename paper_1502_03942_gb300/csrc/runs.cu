@@ -212,6 +212,8 @@ __device__ void runs_decide(const RunsArgs& a, RunsSmem& sm) {
 }
 
 __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_init(RunsArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     __shared__ RunsSmem sm;
     RunsState* st = a.st;
     const u64 total = a.off[a.p];
@@ -250,6 +252,8 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_init(RunsArgs a) {
 
 // Optional order check: every run non-decreasing (one block per run).
 __global__ void __launch_bounds__(RUN_NT) k_runs_check_sorted(RunsArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     const u32 r = blockIdx.x;
     const u64 s = a.off[r], e = a.off[r + 1];
     for (u64 i = s + 1 + threadIdx.x; i < e; i += blockDim.x)
@@ -261,6 +265,8 @@ __global__ void __launch_bounds__(RUN_NT) k_runs_check_sorted(RunsArgs a) {
 
 // One pivot per block: rank of v_j among the undecided objects.
 __global__ void __launch_bounds__(RUN_NT) k_runs_round(RunsArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     __shared__ RunsSmem sm;
     __shared__ u32 is_last;
     RunsState* st = a.st;
@@ -298,6 +304,8 @@ __global__ void __launch_bounds__(RUN_NT) k_runs_round(RunsArgs a) {
 // Remaining rounds inside one block (rare), then the final selection among
 // at most T undecided objects.
 __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_finish(RunsArgs a) {
+    grid_dep_wait();
+    grid_dep_release();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     typedef Comp<64> C;
     typedef C::t ct;
@@ -468,10 +476,12 @@ extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys
         attr_mask.fetch_or(bit);
     }
     const u32 rounds = runs_rounds_for(p, k, a.d);
-    k_runs_init<<<1, RUN_FIN_NT, 0, st>>>(a);
-    if (prm.flags & TOPK_FLAG_CHECK_SORTED) k_runs_check_sorted<<<p, RUN_NT, 0, st>>>(a);
-    for (u32 r = 0; r < rounds; ++r) k_runs_round<<<a.d, RUN_NT, 0, st>>>(a);
-    k_runs_finish<<<1, RUN_FIN_NT, fin_smem, st>>>(a);
+    cudaError_t e = launch_dep(k_runs_init, 1, RUN_FIN_NT, 0, st, a);
+    if (e == cudaSuccess && (prm.flags & TOPK_FLAG_CHECK_SORTED))
+        e = launch_dep(k_runs_check_sorted, (int)p, RUN_NT, 0, st, a);
+    for (u32 r = 0; r < rounds && e == cudaSuccess; ++r) e = launch_dep(k_runs_round, (int)a.d, RUN_NT, 0, st, a);
+    if (e == cudaSuccess) e = launch_dep(k_runs_finish, 1, RUN_FIN_NT, fin_smem, st, a);
+    if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx, 2 + rounds + ((prm.flags & TOPK_FLAG_CHECK_SORTED) ? 1 : 0));
     return cuda_status(cudaGetLastError());
 }

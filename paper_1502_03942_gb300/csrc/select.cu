@@ -1000,23 +1000,6 @@ static u64 candidate_capacity(u64 n, u64 k, const Tuning& tu) {
     return (cap + 4095) & ~(u64)4095;
 }
 
-// Launch with programmatic stream serialization (see grid_dep_wait).
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
-                              Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
 // Enqueues one selection whose state, error word and buffers `a` already
 // points to.  k = 1 and k = n need `counter` (zero) and `partials`
 // (EXT grid composites).  `ctx` (may be null) receives the measurement hooks.
@@ -1072,6 +1055,23 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     return cuda_status(cudaGetLastError());
 }
 
+// Scratch regions of one selection: reduction partials, the sample, and the
+// two candidate buffers (keys, then positions) of `cap` pairs each.
+struct SelectCarve {
+    size_t part, samp, k0, k1, i0, i1;
+};
+template <int KW> static Carve select_carve(u64 cap, int sms, SelectCarve& sc) {
+    const size_t kbytes = KW / 8;
+    Carve cv;
+    sc.part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)sms * EXT_BLOCKS_PER_SM);
+    sc.samp = cv.take(sizeof(typename Comp<KW>::t) * (size_t)Lim<KW>::ELEMS);
+    sc.k0 = cv.take(cap * kbytes);
+    sc.k1 = cv.take(cap * kbytes);
+    sc.i0 = cv.take(cap * 4);
+    sc.i1 = cv.take(cap * 4);
+    return cv;
+}
+
 template <int DT>
 static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_keys, u32* out_idx,
                               void* kth_key, u32* kth_idx, const topk_params* prm, cudaStream_t st) {
@@ -1084,12 +1084,10 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
 
     const u64 cap = (k == 1 || k == n) ? 0 : candidate_capacity(n, k, tu);
     a.cap_b = cap;
-    const size_t kbytes = KW / 8;
-    Carve cv;
-    const size_t off_part = cv.take(sizeof(typename Comp<KW>::t) * (size_t)ctx->sms * EXT_BLOCKS_PER_SM);
-    const size_t off_samp = cv.take(sizeof(typename Comp<KW>::t) * (size_t)Lim<KW>::ELEMS);
-    const size_t off_k0 = cv.take(cap * kbytes), off_k1 = cv.take(cap * kbytes);
-    const size_t off_i0 = cv.take(cap * 4), off_i1 = cv.take(cap * 4);
+    SelectCarve sc;
+    const Carve cv = select_carve<KW>(cap, ctx->sms, sc);
+    const size_t off_part = sc.part, off_samp = sc.samp, off_k0 = sc.k0, off_k1 = sc.k1, off_i0 = sc.i0,
+                 off_i1 = sc.i1;
     topk_status rs = ensure_scratch(ctx, cv.off);
     if (rs != TOPK_OK) return rs;
     char* base = static_cast<char*>(ctx->scratch.base);
@@ -1237,18 +1235,15 @@ topk_status topk_ctx_reserve(topk_ctx* ctx, uint64_t n, topk_dtype dtype) {
     const int w = dtype_bytes(dtype);
     if (w == 0 || n == 0) return TOPK_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
-    const u32 ELEMS = w == 8 ? Lim<64>::ELEMS : Lim<32>::ELEMS;
-    const size_t kbytes = w == 8 ? 8 : 4;
-    // worst first bracket over k (k = n/2), default tuning
-    u64 cap = (u64)(2.0 * est_bracket(n, std::max<u64>(1, n / 2), ELEMS, 4.0f)) + 4ull * ELEMS;
-    cap = std::min<u64>(cap, std::max<u64>(n, ELEMS));
-    cap = (cap + 4095) & ~(u64)4095;
-    Carve cv;
-    cv.take(cap * kbytes);
-    cv.take(cap * kbytes);
-    cv.take(cap * 4);
-    cv.take(cap * 4);
-    return ensure_scratch(ctx, cv.off);
+    // the regions of run_select with the worst first bracket over k (k = n/2)
+    // and the default tuning
+    SelectCarve sc;
+    if (w == 8) {
+        const Tuning tu = make_tuning<64>(nullptr, ctx->sms);
+        return ensure_scratch(ctx, select_carve<64>(candidate_capacity(n, std::max<u64>(2, n / 2), tu), ctx->sms, sc).off);
+    }
+    const Tuning tu = make_tuning<32>(nullptr, ctx->sms);
+    return ensure_scratch(ctx, select_carve<32>(candidate_capacity(n, std::max<u64>(2, n / 2), tu), ctx->sms, sc).off);
 }
 
 topk_status topk_last_stats(topk_ctx* ctx, topk_stats* out) {

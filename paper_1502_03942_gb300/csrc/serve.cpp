@@ -30,6 +30,7 @@ namespace {
 using topk::BATCH_ROW_MAX;
 
 constexpr uint32_t MAX_BATCH_ROWS = 2048;
+constexpr uint64_t RESERVE_N = 1ull << 26;  // selection size each slot's scratch is reserved for
 constexpr uint64_t REQUEST_OVERHEAD = 4096; // state and bookkeeping per request
 
 uint64_t steady_ns() {
@@ -54,6 +55,7 @@ struct Slot {
     uint64_t bytes = 0;
     char* h_ptrs = nullptr; // pinned staging of the batched pointer arrays
     char* d_ptrs = nullptr;
+    uint32_t* h_err = nullptr; // pinned copy of the context's error word, read after each dispatch
 };
 
 uint64_t request_bytes(const topk_request& r) {
@@ -109,6 +111,10 @@ topk_status dispatch(topk_server* s, Slot& slot) {
         if (cudaMemcpyAsync(slot.d_ptrs, h, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rs = TOPK_ECUDA;
         if (rs == TOPK_OK) rs = topk::batched_by_pointers(slot.ctx, w[0].r.dtype, rows, slot.d_ptrs, st);
     }
+    // the device status travels with the work: no blocking read when it retires
+    if (rs == TOPK_OK && cudaMemcpyAsync(slot.h_err, slot.ctx->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                         st) != cudaSuccess)
+        rs = TOPK_ECUDA;
     if (cudaEventRecord(slot.done, st) != cudaSuccess && rs == TOPK_OK) rs = TOPK_ECUDA;
     return rs;
 }
@@ -125,8 +131,12 @@ void worker_main(topk_server* s) {
                 any_busy = true;
                 continue;
             }
-            topk_status rs = q == cudaSuccess ? topk_status_sync(slot.ctx, slot.stream) : TOPK_ECUDA;
+            topk_status rs = q == cudaSuccess ? static_cast<topk_status>(*slot.h_err) : TOPK_ECUDA;
             if (q != cudaSuccess) cudaGetLastError();
+            if (rs != TOPK_OK && q == cudaSuccess) { // clear it before the slot's next work (stream order)
+                *slot.h_err = 0;
+                cudaMemsetAsync(slot.ctx->d_err, 0, sizeof(uint32_t), slot.stream);
+            }
             const uint64_t now = steady_ns();
             std::lock_guard<std::mutex> lock(s->mu);
             for (const Pending& p : slot.work) {
@@ -198,7 +208,9 @@ void worker_main(topk_server* s) {
                 s->cv_done.notify_all();
             }
         }
-        if (launch.empty()) std::this_thread::sleep_for(std::chrono::microseconds(5));
+        // slots are busy: poll again soon (a sleep would cost tens of
+        // microseconds of timer slack on every completion)
+        if (launch.empty()) std::this_thread::yield();
     }
 }
 
@@ -218,9 +230,15 @@ topk_status topk_serve_create(topk_server** out, int device, uint64_t hbm_budget
     for (Slot& slot : s->slots) {
         if (rs != TOPK_OK) break;
         if ((rs = topk_ctx_create(&slot.ctx, device)) != TOPK_OK) break;
+        // scratch for the largest work a slot usually gets (a selection of
+        // 2^26 keys, a batch of MAX_BATCH_ROWS rows, 64-bit keys), so that
+        // growing it -- which synchronises the device -- stays rare
+        if ((rs = topk_ctx_reserve(slot.ctx, RESERVE_N, TOPK_U64)) != TOPK_OK) break;
+        if ((rs = topk::batched_reserve(slot.ctx, TOPK_U64, MAX_BATCH_ROWS)) != TOPK_OK) break;
         if (cudaStreamCreateWithFlags(&slot.stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&slot.done, cudaEventDisableTiming) != cudaSuccess ||
             cudaMallocHost(reinterpret_cast<void**>(&slot.h_ptrs), 52ull * MAX_BATCH_ROWS) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&slot.h_err), sizeof(uint32_t)) != cudaSuccess ||
             cudaMalloc(reinterpret_cast<void**>(&slot.d_ptrs), 52ull * MAX_BATCH_ROWS) != cudaSuccess)
             rs = TOPK_ENOMEM;
     }
@@ -297,6 +315,27 @@ topk_status topk_serve_stats(topk_server* s, topk_serve_report* out) {
     return TOPK_OK;
 }
 
+topk_status topk_serve_replay(topk_server* s, const topk_request* reqs, const int64_t* done_before, uint64_t count,
+                              uint64_t* tickets, uint64_t* lag_ns) {
+    if (!s || (count && (!reqs || !done_before || !tickets))) return TOPK_EINVAL;
+    int64_t waited = -1; // every request of index <= waited has finished
+    for (uint64_t i = 0; i < count; ++i) {
+        const int64_t need = done_before[i];
+        if (need >= (int64_t)i) return TOPK_EINVAL; // only earlier requests can be waited for
+        while (waited < need) {
+            ++waited;
+            if (tickets[waited] == 0) continue; // rejected at submission
+            const topk_status st = topk_serve_wait(s, tickets[waited], 60ull * 1000 * 1000 * 1000);
+            if (st == TOPK_ETIMEOUT) return TOPK_ETIMEOUT;
+        }
+        uint64_t now = steady_ns();
+        while (now < reqs[i].arrival_ns) now = steady_ns();
+        if (lag_ns) lag_ns[i] = now - (reqs[i].arrival_ns ? reqs[i].arrival_ns : now);
+        if (topk_serve_submit(s, &reqs[i], &tickets[i]) != TOPK_OK) tickets[i] = 0;
+    }
+    return TOPK_OK;
+}
+
 uint64_t topk_serve_now_ns(topk_server* s) {
     (void)s;
     return steady_ns();
@@ -318,6 +357,7 @@ void topk_serve_destroy(topk_server* s) {
         if (slot.done) cudaEventDestroy(slot.done);
         if (slot.stream) cudaStreamDestroy(slot.stream);
         if (slot.h_ptrs) cudaFreeHost(slot.h_ptrs);
+        if (slot.h_err) cudaFreeHost(slot.h_err);
         if (slot.d_ptrs) cudaFree(slot.d_ptrs);
         if (slot.ctx) topk_ctx_destroy(slot.ctx);
     }

@@ -142,3 +142,49 @@ def test_serve_wait_timeout_and_bad_request(tk):
         srv.submit(keys, 0, out)
     assert e.value.status == tk.TOPK_EINVAL
     srv.close()
+
+
+def test_replay_trace_with_output_reuse(tk):
+    """topk_serve_replay submits a trace natively; requests 30..59 reuse the
+    outputs of requests 0..29 and must wait for them: the final outputs are
+    those of the later requests, each equal to the oracle's."""
+    import torch
+    g = np.random.Generator(np.random.Philox(65))
+    srv = tk.Server(0, hbm_budget=1 << 30, max_slots=4)
+    reqs_host = [make_request(g, 10, 16) for _ in range(60)]
+    keys = [to_device(b, nm) for b, nm, _ in reqs_host]
+    def shared_outputs(kmax):  # room for either key width
+        return (torch.empty(4 * kmax, dtype=torch.uint8, device="cuda"),
+                torch.empty(kmax, dtype=torch.uint32, device="cuda"),
+                torch.empty(16, dtype=torch.uint8, device="cuda"),
+                torch.empty(1, dtype=torch.uint32, device="cuda"))
+    outs = [shared_outputs(max(reqs_host[i][2], reqs_host[i + 30][2])) for i in range(30)]
+    torch.cuda.synchronize()
+    reqs = np.zeros(60, dtype=np.dtype(tk.topk_request))
+    done_before = np.full(60, -1, np.int64)
+    for i in range(60):
+        o = outs[i % 30]
+        reqs[i]["d_keys"] = keys[i].data_ptr()
+        reqs[i]["n"] = keys[i].numel()
+        reqs[i]["k"] = reqs_host[i][2]
+        reqs[i]["dtype"] = tk.dtype_code(keys[i])
+        reqs[i]["d_out_keys"] = o[0].data_ptr()
+        reqs[i]["d_out_idx"] = o[1].data_ptr()
+        reqs[i]["d_kth_key"] = o[2].data_ptr()
+        reqs[i]["d_kth_idx"] = o[3].data_ptr()
+        if i >= 30:
+            done_before[i] = i - 30
+    tickets, lags = srv.replay(reqs, done_before)
+    assert all(int(t) > 0 for t in tickets)
+    for t in tickets:
+        assert srv.wait(int(t)) == tk.TOPK_OK
+    for i in range(30, 60):
+        bits, name, k = reqs_host[i]
+        o = outs[i - 30]
+        idx = bits_of(o[1])[:k]
+        want_sel, want_kth = oracle.select(bits, name, k)
+        assert np.array_equal(np.sort(idx), np.sort(want_sel))
+        assert int(bits_of(o[3])[0]) == want_kth
+    with pytest.raises(tk.TopkError):
+        srv.replay(reqs[:2], np.array([-1, 1], np.int64))  # may only wait for earlier requests
+    srv.close()

@@ -341,7 +341,8 @@ def measure_sorted_runs(tk, wl, torch, ctx):
     d_keys = torch.from_numpy(keys.view(np.int64)).cuda().view(torch.uint64)
     d_off = torch.from_numpy(off.view(np.int64)).cuda().view(torch.uint64)
     total = int(off[-1])
-    res = {"workload": "1024 sorted u64 runs, lengths 2^U(10,20), k in {1, 2^16, total/2}", "total": total}
+    res = {"workload": "1024 sorted u64 runs, lengths 2^U(10,20), k in {1, 2^16, total/2}; "
+                       "flexible k in [k, 1.1 k] for k in {2^16, total/2}", "total": total}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, k in (("k1", 1), ("k65536", 1 << 16), ("half", total // 2)):
         out = tk.topk_select_sorted_runs(ctx, d_keys, d_off, k)
@@ -356,6 +357,22 @@ def measure_sorted_runs(tk, wl, torch, ctx):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3)}
+    # flexible k (amsSelect): any k within 10% above the same targets
+    for name, kmin in (("flex_k65536", 1 << 16), ("flex_half", total // 2)):
+        kmax = kmin + kmin // 10
+        out = tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax)
+        for _ in range(2):
+            tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax, out=out, check=False)
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3), "kmin": kmin, "kmax": kmax,
+                     "k": int(out[4].cpu().view(torch.int64)[0])}
     res["status"] = ctx.sync()
     return res
 

@@ -154,6 +154,31 @@ topk_status topk_select_sorted_runs(topk_ctx *ctx, const void *d_keys,
                                     uint64_t *d_kth_pos, const topk_params *params,
                                     void *stream);
 
+/* Flexible-k multisequence selection (Section 4.3, Algorithm amsSelect, with
+ * d concurrent trials per round as in "Multiple Concurrent Trials"): selects
+ * the k smallest objects of the p sorted runs for some k with
+ * kmin <= k <= kmax that the search finds first, and reports that k.  Each
+ * trial estimates an object of rank in [kmin, kmax] as the minimum over the
+ * runs of each run's x-th smallest undecided object (x a geometric deviate
+ * with the success rate the paper derives), or the maximum of x-th largest
+ * ones when the range lies in the upper part; a trial whose exact rank falls
+ * in the range ends the search, otherwise the tightest under- and
+ * over-estimates narrow every run's bracket.  The result is exact for the k
+ * returned: the same objects as topk_select_sorted_runs with that k.
+ *   Arguments as topk_select_sorted_runs, with 1 <= kmin <= kmax < 2^32
+ *   (kmin > off[p] is reported by topk_status_sync() as TOPK_EINVAL; kmax
+ *   above off[p] is clamped to it) and
+ *   d_k        1 uint64 (caller-owned device memory): the k chosen.
+ * params->sample_size, when set, is the number of trials per round
+ * (default 64, at most 256); params->seed seeds the deviates.  Which k is
+ * chosen depends on the seed and on d; the selection for that k does not. */
+topk_status topk_select_sorted_runs_flexible(topk_ctx *ctx, const void *d_keys,
+                                             const uint64_t *d_run_off, uint32_t p, uint64_t kmin,
+                                             uint64_t kmax, topk_dtype dtype, uint64_t *d_split,
+                                             void *d_kth_key, uint32_t *d_kth_run,
+                                             uint64_t *d_kth_pos, uint64_t *d_k,
+                                             const topk_params *params, void *stream);
+
 /* Many independent selections in one persistent launch (no counterpart in the
  * paper: it is the selection of Section 2 run once per row).
  *   d_keys     all rows back to back, `dtype`.

@@ -88,6 +88,9 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_sorted_runs"):
         lib.topk_select_sorted_runs.argtypes = [vp, vp, vp, u32, u64, i32, vp, vp, vp, vp, vp, vp]
         lib.topk_select_sorted_runs.restype = st
+    if hasattr(lib, "topk_select_sorted_runs_flexible"):
+        lib.topk_select_sorted_runs_flexible.argtypes = [vp, vp, vp, u32, u64, u64, i32, vp, vp, vp, vp, vp, vp, vp]
+        lib.topk_select_sorted_runs_flexible.restype = st
     if hasattr(lib, "topk_select_batched"):
         lib.topk_select_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_batched.restype = st
@@ -277,6 +280,32 @@ def topk_select_sorted_runs(ctx: Context, keys, run_off, k: int, params: topk_pa
     _check(st, "topk_select_sorted_runs")
     if check:
         _check(ctx.sync(stream), "topk_select_sorted_runs (device)")
+    return out
+
+
+def topk_select_sorted_runs_flexible(ctx: Context, keys, run_off, kmin: int, kmax: int,
+                                     params: topk_params | None = None, stream=None, out=None, check: bool = True):
+    """The k smallest over p sorted runs for some k in [kmin, kmax] (amsSelect).
+
+    Returns (split[p] uint64, kth_key[1] uint64, kth_run[1] uint32,
+    kth_pos[1] uint64, k[1] uint64)."""
+    torch = _torch()
+    if keys.dtype != torch.uint64 or run_off.dtype != torch.uint64:
+        raise TypeError("keys and run_off must be uint64 tensors")
+    p = run_off.numel() - 1
+    if out is None:
+        out = (torch.empty(max(p, 1), dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device))
+    split, kk, kr, kp, kout = out
+    st = load_library().topk_select_sorted_runs_flexible(
+        ctx.handle, _ptr(keys), _ptr(run_off), p, int(kmin), int(kmax), TOPK_U64, _ptr(split), _ptr(kk), _ptr(kr),
+        _ptr(kp), _ptr(kout), ctypes.byref(params) if params is not None else None, _stream_ptr(stream))
+    _check(st, "topk_select_sorted_runs_flexible")
+    if check:
+        _check(ctx.sync(stream), "topk_select_sorted_runs_flexible (device)")
     return out
 
 

@@ -41,6 +41,8 @@ struct RunsState {
     u64 total;    // objects in all runs
     u64 k_rem;    // rank (1-based) sought among the undecided objects
     u64 m;        // undecided objects
+    u64 kmin, kmax; // flexible k: the range still allowed, counted among the undecided objects
+    u64 committed;  // objects already selected (below every lo_r)
     u32 phase, round, status, rounds_grid;
     u32 rounds_block, pad0;
 };
@@ -68,7 +70,13 @@ struct RunsArgs {
     u64* kth_key;   // 1 (caller)
     u32* kth_run;
     u64* kth_pos;
+    // flexible k (Section 4.3, Algorithm amsSelect): any k in [kmin, kmax]
+    u32 flexible;
+    u64 kmin, kmax;
+    u64* k_out;     // 1 (caller): the k chosen
 };
+
+constexpr u64 VOID_PIVOT = ~(u64)0; // a trial whose every run fell short (no estimate)
 
 __device__ inline void runs_latch(const RunsArgs& a, u32 code) {
     atomicCAS(a.err, 0u, code);
@@ -152,6 +160,135 @@ __device__ void draw_pivots(const RunsArgs& a, u64 m, u32 round) {
     }
 }
 
+// Geometric deviate on {1, 2, ...} with ln(1 - q) = ln_keep (<= 0): the
+// number of Bernoulli(q) trials up to the first success, from one uniform
+// variate by inversion.  ln_keep = -inf (q = 1) gives 1.
+__device__ __forceinline__ u64 geometric_deviate(u32 bits, float ln_keep) {
+    if (isinf(ln_keep)) return 1;                  // q = 1
+    if (!(ln_keep < 0.f)) return ~(u64)0;          // q = 0: never
+    const float u = ((float)(bits >> 8) + 0.5f) * (1.0f / 16777216.0f); // (0, 1)
+    const float x = floorf(logf(u) / ln_keep);
+    return x >= 1.8e19f ? ~(u64)0 : (u64)x + 1;
+}
+
+// The d trials of a flexible round (Section 4.3, Algorithm amsSelect with
+// "Multiple Concurrent Trials"): in every run r, trial j draws a geometric
+// deviate x and takes the run's x-th smallest undecided object (min-based
+// estimator) or its x-th largest (max-based estimator, used when the range
+// sought lies in the upper half); the trial's estimate is the minimum
+// (maximum) of those over all runs, an object whose rank is most likely in
+// [kmin, kmax].  One warp per trial.
+__device__ void draw_flexible(const RunsArgs& a, const RunsState& st, u32 round) {
+    const u64 m = st.m, kmin = st.kmin, kmax = st.kmax;
+    const bool min_based = kmin < m - (kmax < m ? kmax : m);
+    // ln(1 - q): q = 1 - ((kmin-1)/kmax)^(1/(kmax-kmin+1)), or for the
+    // max-based estimator q = 1 - ((m-kmax)/(m-kmin+1))^(1/(kmax-kmin+1))
+    // (as log1p of the complement, accurate when the ratio is close to 1)
+    const float span = (float)(kmax - kmin + 1);
+    const float ln_keep = min_based ? log1pf(-span / (float)kmax) / span
+                                    : log1pf(-span / (float)(m - kmin + 1)) / span;
+    const u32 lane = lane_id(), nwarps = blockDim.x >> 5;
+    for (u32 j = threadIdx.x >> 5; j < a.d; j += nwarps) {
+        u64 bk = min_based ? ~(u64)0 : 0, bg = VOID_PIVOT;
+        u32 br = 0;
+        constexpr u32 B = 8; // runs per lane whose loads are in flight together
+        for (u32 r0 = lane; r0 < a.p; r0 += 32 * B) {
+            u64 gg[B], kk[B];
+#pragma unroll
+            for (u32 b = 0; b < B; ++b) {
+                const u32 r = r0 + 32 * b;
+                gg[b] = VOID_PIVOT;
+                if (r < a.p) {
+                    const u64 lo = a.lo[r], hi = a.hi[r];
+                    const Philox4 rr = philox4x32_10(r, j, round, 0x414D5345u, (u32)a.seed, (u32)(a.seed >> 32));
+                    const u64 x = geometric_deviate(rr.v[0], ln_keep);
+                    if (x <= hi - lo) gg[b] = a.off[r] + (min_based ? lo + x - 1 : hi - x);
+                }
+            }
+#pragma unroll
+            for (u32 b = 0; b < B; ++b) kk[b] = gg[b] != VOID_PIVOT ? a.keys[gg[b]] : 0;
+#pragma unroll
+            for (u32 b = 0; b < B; ++b) {
+                if (gg[b] == VOID_PIVOT) continue;
+                const bool better = bg == VOID_PIVOT ||
+                                    (min_based ? pair_less(kk[b], gg[b], bk, bg) : pair_less(bk, bg, kk[b], gg[b]));
+                if (better) {
+                    bk = kk[b];
+                    bg = gg[b];
+                    br = r0 + 32 * b;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const u64 ok = __shfl_xor_sync(0xffffffffu, bk, o), og = __shfl_xor_sync(0xffffffffu, bg, o);
+            const u32 orr = __shfl_xor_sync(0xffffffffu, br, o);
+            const bool take = og != VOID_PIVOT &&
+                              (bg == VOID_PIVOT || (min_based ? pair_less(ok, og, bk, bg) : pair_less(bk, bg, ok, og)));
+            if (take) {
+                bk = ok;
+                bg = og;
+                br = orr;
+            }
+        }
+        if (lane == 0) {
+            a.piv_key[j] = bk;
+            a.piv_g[j] = bg;
+            a.piv_run[j] = br;
+        }
+    }
+}
+
+// Trial j's estimate, drawn by a whole block (the round kernel, one block
+// per trial): every thread takes some runs, the block reduces to the
+// minimum (maximum) pair.  Result in piv_*[j].
+__device__ void draw_flexible_block(const RunsArgs& a, const RunsState& st, u32 j, u32 round, u64* red_k, u64* red_g,
+                                    u32* red_r) {
+    const u64 m = st.m, kmin = st.kmin, kmax = st.kmax;
+    const bool min_based = kmin < m - (kmax < m ? kmax : m);
+    const float span = (float)(kmax - kmin + 1);
+    const float ln_keep = min_based ? log1pf(-span / (float)kmax) / span
+                                    : log1pf(-span / (float)(m - kmin + 1)) / span;
+    const u32 lane = lane_id(), warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    u64 bk = min_based ? ~(u64)0 : 0, bg = VOID_PIVOT;
+    u32 br = 0;
+    auto consider = [&](u64 key, u64 g, u32 r) {
+        if (g == VOID_PIVOT) return;
+        if (bg == VOID_PIVOT || (min_based ? pair_less(key, g, bk, bg) : pair_less(bk, bg, key, g))) {
+            bk = key;
+            bg = g;
+            br = r;
+        }
+    };
+    for (u32 r = threadIdx.x; r < a.p; r += blockDim.x) {
+        const u64 lo = a.lo[r], hi = a.hi[r];
+        const Philox4 rr = philox4x32_10(r, j, round, 0x414D5345u, (u32)a.seed, (u32)(a.seed >> 32));
+        const u64 x = geometric_deviate(rr.v[0], ln_keep);
+        if (x > hi - lo) continue;
+        const u64 g = a.off[r] + (min_based ? lo + x - 1 : hi - x);
+        consider(a.keys[g], g, r);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 ok = __shfl_xor_sync(0xffffffffu, bk, o), og = __shfl_xor_sync(0xffffffffu, bg, o);
+        const u32 orr = __shfl_xor_sync(0xffffffffu, br, o);
+        consider(ok, og, orr);
+    }
+    if (lane == 0) {
+        red_k[warp] = bk;
+        red_g[warp] = bg;
+        red_r[warp] = br;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (u32 w = 1; w < nw; ++w) consider(red_k[w], red_g[w], red_r[w]);
+        a.piv_key[j] = bk;
+        a.piv_g[j] = bg;
+        a.piv_run[j] = br;
+    }
+    __syncthreads();
+}
+
 struct RunsSmem {
     u64 warp_sums[RUN_FIN_NT / 32 + 1];
     u64 carry;
@@ -165,14 +302,24 @@ __device__ void runs_decide(const RunsArgs& a, RunsSmem& sm) {
     RunsState* st = a.st;
     const u32 tid = threadIdx.x;
     if (tid == 0) {
-        const u64 target = st->k_rem - 1; // undecided objects below the k-th
+        // the undecided objects below the pivot sought: exactly k_rem - 1, or
+        // (flexible) any number in [kmin - 1, kmax - 1]
+        const u64 tlo = a.flexible ? st->kmin - 1 : st->k_rem - 1;
+        const u64 thi = a.flexible ? st->kmax - 1 : st->k_rem - 1;
         int bl = -1, bh = -1, ex = -1;
         u64 rl = 0, rh = ~(u64)0;
         for (u32 j = 0; j < a.d; ++j) {
+            if (__ldcg(a.piv_g + j) == VOID_PIVOT) continue;
             const u64 rj = __ldcg(a.piv_rank + j);
-            if (rj == target) ex = (int)j;
-            else if (rj < target && (bl < 0 || rj > rl)) { bl = (int)j; rl = rj; }
-            else if (rj > target && (bh < 0 || rj < rh)) { bh = (int)j; rh = rj; }
+            if (rj >= tlo && rj <= thi) {
+                if (ex < 0) ex = (int)j;
+            } else if (rj < tlo && (bl < 0 || rj > rl)) {
+                bl = (int)j;
+                rl = rj;
+            } else if (rj > thi && (bh < 0 || rj < rh)) {
+                bh = (int)j;
+                rh = rj;
+            }
         }
         sm.best_lo = bl;
         sm.best_hi = bh;
@@ -188,6 +335,7 @@ __device__ void runs_decide(const RunsArgs& a, RunsSmem& sm) {
             *a.kth_key = a.piv_key[ex];
             *a.kth_run = vr;
             *a.kth_pos = a.piv_g[ex] - a.off[vr];
+            if (a.k_out) *a.k_out = st->committed + __ldcg(a.piv_rank + ex) + 1;
             st->phase = RPH_DONE;
         }
         __syncthreads();
@@ -201,13 +349,26 @@ __device__ void runs_decide(const RunsArgs& a, RunsSmem& sm) {
     __syncthreads();
     const u64 m = block_prefix_brackets(a, sm.warp_sums, &sm.carry);
     if (tid == 0) {
-        if (bl >= 0) st->k_rem -= __ldcg(a.piv_rank + bl) + 1;
+        if (bl >= 0) {
+            const u64 below = __ldcg(a.piv_rank + bl) + 1; // now selected
+            st->k_rem -= below;
+            st->committed += below;
+            if (a.flexible) {
+                st->kmin -= below;
+                st->kmax -= below;
+            }
+        }
+        if (a.flexible) {
+            if (st->kmax > m) st->kmax = m;
+            st->k_rem = st->kmin; // what the one-block finish selects
+        }
         st->m = m;
         st->round += 1;
         if (m <= RUN_T) st->phase = RPH_FINISH;
     }
     __syncthreads();
-    if (st->phase == RPH_RUN) draw_pivots(a, m, st->round);
+    // (flexible trials are drawn by the next round's blocks, one per trial)
+    if (st->phase == RPH_RUN && !a.flexible) draw_pivots(a, m, st->round);
     __syncthreads();
 }
 
@@ -219,14 +380,17 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_init(RunsArgs a) {
     const u64 total = a.off[a.p];
     if (threadIdx.x == 0) {
         st->total = total;
-        st->k_rem = a.k;
+        st->k_rem = a.flexible ? a.kmin : a.k;
+        st->kmin = a.flexible ? a.kmin : a.k;
+        st->kmax = a.flexible ? a.kmax : a.k;
+        st->committed = 0;
         st->round = 0;
         st->status = 0;
         st->rounds_grid = 0;
         st->rounds_block = 0;
         st->phase = RPH_RUN;
         sm.flag = 1;
-        if (a.off[0] != 0 || a.k > total || total > 0xFFFFFFFFull) {
+        if (a.off[0] != 0 || (a.flexible ? a.kmin : a.k) > total || total > 0xFFFFFFFFull) {
             runs_latch(a, ST_EINVAL);
             sm.flag = 0;
         }
@@ -237,17 +401,19 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_init(RunsArgs a) {
         const u64 s = a.off[r], e = a.off[r + 1];
         const u64 len = e >= s ? e - s : 0;
         a.lo[r] = 0;
-        a.hi[r] = len < a.k ? len : a.k; // only the first k of a run can be selected
+        const u64 kcap = a.flexible ? a.kmax : a.k;
+        a.hi[r] = len < kcap ? len : kcap; // only the first k of a run can be selected
         if (e < s) runs_latch(a, ST_EINVAL);
     }
     __syncthreads();
     const u64 m = block_prefix_brackets(a, sm.warp_sums, &sm.carry);
     if (threadIdx.x == 0) {
         st->m = m;
+        if (a.flexible && st->kmax > m) st->kmax = m;
         if (st->phase == RPH_RUN && m <= RUN_T) st->phase = RPH_FINISH;
     }
     __syncthreads();
-    if (st->phase == RPH_RUN) draw_pivots(a, m, 0);
+    if (st->phase == RPH_RUN && !a.flexible) draw_pivots(a, m, 0);
 }
 
 // Optional order check: every run non-decreasing (one block per run).
@@ -269,17 +435,21 @@ __global__ void __launch_bounds__(RUN_NT) k_runs_round(RunsArgs a) {
     grid_dep_release();
     __shared__ RunsSmem sm;
     __shared__ u32 is_last;
+    __shared__ u64 red_k[RUN_NT / 32], red_g[RUN_NT / 32];
+    __shared__ u32 red_r[RUN_NT / 32];
     RunsState* st = a.st;
     if (st->phase != RPH_RUN) return;
     const u32 j = blockIdx.x;
+    if (a.flexible) draw_flexible_block(a, *st, j, st->round, red_k, red_g, red_r);
     const u64 vk = a.piv_key[j], vg = a.piv_g[j];
     u64 acc = 0;
-    for (u32 r = threadIdx.x; r < a.p; r += blockDim.x) {
-        const u64 lo = a.lo[r], hi = a.hi[r], base = a.off[r];
-        const u64 c = count_below(a.keys, base, lo, hi, vk, vg) - lo;
-        a.cnt[(size_t)j * a.p + r] = (u32)c;
-        acc += c;
-    }
+    if (vg != VOID_PIVOT) // (a void trial has no estimate to rank)
+        for (u32 r = threadIdx.x; r < a.p; r += blockDim.x) {
+            const u64 lo = a.lo[r], hi = a.hi[r], base = a.off[r];
+            const u64 c = count_below(a.keys, base, lo, hi, vk, vg) - lo;
+            a.cnt[(size_t)j * a.p + r] = (u32)c;
+            acc += c;
+        }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane_id() == 0) sm.red[threadIdx.x >> 5] = acc;
@@ -315,10 +485,14 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_finish(RunsArgs a) {
     __shared__ RadixSmem<64, 1> rs;
     RunsState* st = a.st;
     for (u32 it = 0; it < RUN_MAX_BLOCK_ROUNDS && st->phase == RPH_RUN; ++it) {
+        if (a.flexible) {
+            draw_flexible(a, *st, st->round);
+            __syncthreads();
+        }
         for (u32 j = 0; j < a.d; ++j) { // one block does every pivot
             const u64 vk = a.piv_key[j], vg = a.piv_g[j];
             u64 acc = 0;
-            for (u32 r = threadIdx.x; r < a.p; r += blockDim.x) {
+            for (u32 r = threadIdx.x; r < a.p && vg != VOID_PIVOT; r += blockDim.x) {
                 const u64 lo = a.lo[r];
                 const u64 c = count_below(a.keys, a.off[r], lo, a.hi[r], vk, vg) - lo;
                 a.cnt[(size_t)j * a.p + r] = (u32)c;
@@ -379,6 +553,7 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_finish(RunsArgs a) {
         *a.kth_key = C::key(kth);
         *a.kth_run = lo;
         *a.kth_pos = kg - a.off[lo];
+        if (a.k_out) *a.k_out = st->committed + st->k_rem;
     }
     // splits: lo_r plus the undecided objects of run r not above the k-th,
     // counted in chunks of RUN_FIN_NT runs
@@ -421,12 +596,17 @@ static u32 runs_rounds_for(u64 p, u64 k, u32 d) {
 
 using namespace topk;
 
-extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off,
-                                               uint32_t p, uint64_t k, topk_dtype dtype, uint64_t* d_split,
-                                               void* d_kth_key, uint32_t* d_kth_run, uint64_t* d_kth_pos,
-                                               const topk_params* params, void* stream) {
+namespace topk {
+
+// Both entry points: exact k (flexible = false) or any k in [kmin, kmax].
+static topk_status run_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off, uint32_t p,
+                                   uint64_t k, bool flexible, uint64_t kmin, uint64_t kmax, topk_dtype dtype,
+                                   uint64_t* d_split, void* d_kth_key, uint32_t* d_kth_run, uint64_t* d_kth_pos,
+                                   uint64_t* d_k, const topk_params* params, void* stream) {
     if (!ctx || !d_keys || !d_run_off || !d_split || !d_kth_key || !d_kth_run || !d_kth_pos) return TOPK_EINVAL;
-    if (dtype != TOPK_U64 || p == 0 || p > (1u << 24) || k == 0 || k > 0xFFFFFFFFull) return TOPK_EINVAL;
+    if (flexible && (!d_k || kmin == 0 || kmin > kmax || kmax > 0xFFFFFFFFull)) return TOPK_EINVAL;
+    if (!flexible && (k == 0 || k > 0xFFFFFFFFull)) return TOPK_EINVAL;
+    if (dtype != TOPK_U64 || p == 0 || p > (1u << 24)) return TOPK_EINVAL;
     if (reinterpret_cast<uintptr_t>(d_keys) % 8 || reinterpret_cast<uintptr_t>(d_run_off) % 8) return TOPK_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     topk_params prm{};
@@ -436,7 +616,11 @@ extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys
     a.keys = static_cast<const u64*>(d_keys);
     a.off = d_run_off;
     a.p = p;
-    a.k = k;
+    a.k = flexible ? kmin : k;
+    a.flexible = flexible ? 1u : 0u;
+    a.kmin = kmin;
+    a.kmax = kmax;
+    a.k_out = flexible ? d_k : nullptr;
     a.d = prm.sample_size ? std::min<u32>(std::max<u32>(prm.sample_size, 1), RUN_MAX_D) : 64;
     a.seed = prm.seed ? prm.seed : 0x13198A2E03707344ull;
     a.flags = prm.flags;
@@ -475,7 +659,9 @@ extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys
             return TOPK_ECUDA;
         attr_mask.fetch_or(bit);
     }
-    const u32 rounds = runs_rounds_for(p, k, a.d);
+    // a flexible search usually ends within a round or two (each trial lands
+    // in the range with constant probability); the spare rounds return at once
+    const u32 rounds = flexible ? std::min<u32>(runs_rounds_for(p, kmax, a.d), 4u) : runs_rounds_for(p, k, a.d);
     cudaError_t e = launch_dep(k_runs_init, 1, RUN_FIN_NT, 0, st, a);
     if (e == cudaSuccess && (prm.flags & TOPK_FLAG_CHECK_SORTED))
         e = launch_dep(k_runs_check_sorted, (int)p, RUN_NT, 0, st, a);
@@ -484,4 +670,23 @@ extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys
     if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx, 2 + rounds + ((prm.flags & TOPK_FLAG_CHECK_SORTED) ? 1 : 0));
     return cuda_status(cudaGetLastError());
+}
+
+} // namespace topk
+
+extern "C" topk_status topk_select_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off,
+                                               uint32_t p, uint64_t k, topk_dtype dtype, uint64_t* d_split,
+                                               void* d_kth_key, uint32_t* d_kth_run, uint64_t* d_kth_pos,
+                                               const topk_params* params, void* stream) {
+    return run_sorted_runs(ctx, d_keys, d_run_off, p, k, false, 0, 0, dtype, d_split, d_kth_key, d_kth_run, d_kth_pos,
+                           nullptr, params, stream);
+}
+
+extern "C" topk_status topk_select_sorted_runs_flexible(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off,
+                                                        uint32_t p, uint64_t kmin, uint64_t kmax, topk_dtype dtype,
+                                                        uint64_t* d_split, void* d_kth_key, uint32_t* d_kth_run,
+                                                        uint64_t* d_kth_pos, uint64_t* d_k, const topk_params* params,
+                                                        void* stream) {
+    return run_sorted_runs(ctx, d_keys, d_run_off, p, 0, true, kmin, kmax, dtype, d_split, d_kth_key, d_kth_run,
+                           d_kth_pos, d_k, params, stream);
 }

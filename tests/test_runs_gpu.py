@@ -115,3 +115,80 @@ def test_runs_config_full_size(tk, ctx, kind):
     first_g = starts + split
     fk = keys[first_g[has_rest]]
     assert np.all((fk > kk) | ((fk == kk) & (first_g[has_rest] > g_k)))
+
+
+def run_flexible_and_check(tk, ctx, keys, off, kmin, kmax, params=None):
+    """The k returned lies in [kmin, kmax] (kmax clamped to the total) and the
+    selection equals the oracle's for that k."""
+    d_keys = to_device(keys, "u64")
+    d_off = to_device(off, "u64")
+    split, kk, kr, kp, kout = tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax, params=params)
+    k = int(bits_of(kout)[0])
+    assert kmin <= k <= min(kmax, int(off[-1])), (kmin, kmax, k)
+    want_split, want_run, want_pos = oracle.select_runs(keys, off, k)
+    assert np.array_equal(bits_of(split)[: off.size - 1], want_split), "splits differ"
+    assert int(bits_of(split)[: off.size - 1].sum()) == k
+    assert int(bits_of(kr)[0]) == want_run and int(bits_of(kp)[0]) == want_pos, "rank-k object differs"
+    assert int(bits_of(kk)[0]) == int(keys[int(off[want_run]) + want_pos])
+    return k
+
+
+@pytest.mark.parametrize("p,maxlen", [(1, 50000), (7, 20000), (300, 3000), (1024, 40000)])
+def test_flexible_ranges(tk, ctx, p, maxlen):
+    keys, off = make_runs(p, maxlen, seed=81 + p)
+    total = int(off[-1])
+    ranges = [(1, 1), (1, 10), (100, 200), (total // 3, total // 3 + total // 20), (total // 2, total // 2),
+              (total - 10, total + 1000), (5000, 5000 + 5000 // 64), (1, total)]
+    for kmin, kmax in ranges:
+        kmin = max(1, min(kmin, total))
+        run_flexible_and_check(tk, ctx, keys, off, kmin, max(kmin, kmax))
+
+
+def test_flexible_ties_and_seeds(tk, ctx):
+    """Heavy ties; several seeds and trial counts: the k may differ, the
+    selection for it never does."""
+    keys, off = make_runs(64, 5000, seed=91, alphabet=5)
+    total = int(off[-1])
+    ks = set()
+    for seed, d in ((1, 64), (2, 64), (3, 8), (4, 256)):
+        p = tk.make_params(seed=seed, sample_size=d)
+        ks.add(run_flexible_and_check(tk, ctx, keys, off, total // 4, total // 4 + total // 10, params=p))
+    assert ks
+
+
+def test_flexible_rejects_bad_ranges(tk, ctx):
+    keys, off = make_runs(4, 100, seed=92)
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    for kmin, kmax in ((0, 5), (6, 5)):
+        with pytest.raises(tk.TopkError) as e:
+            tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax)
+        assert e.value.status == tk.TOPK_EINVAL
+
+
+def test_flexible_full_configuration(tk, ctx):
+    """1024 runs of 2^U(10,20) sorted u64 keys, k within 10% above 2^16 and
+    above total/2: in range, and the splits are the k smallest for the k
+    chosen (the properties that fix the answer uniquely)."""
+    keys, off = wl.sorted_runs(1024, 10, 20, seed=3)
+    total = int(off[-1])
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    lens = np.diff(off).astype(np.int64)
+    starts = off[:-1].astype(np.int64)
+    for kmin in (1 << 16, total // 2):
+        kmax = kmin + kmin // 10
+        split, kk, kr, kp, kout = tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax)
+        k = int(bits_of(kout)[0])
+        assert kmin <= k <= kmax
+        split = bits_of(split).astype(np.int64)
+        kr, kp, kk = int(bits_of(kr)[0]), int(bits_of(kp)[0]), int(bits_of(kk)[0])
+        assert split.sum() == k and np.all(split >= 0) and np.all(split <= lens)
+        g_k = int(off[kr]) + kp
+        assert kk == int(keys[g_k]) and split[kr] == kp + 1
+        has_sel = split > 0
+        last_g = starts + split - 1
+        lk = keys[last_g[has_sel]]
+        assert np.all((lk < kk) | ((lk == kk) & (last_g[has_sel] <= g_k)))
+        has_rest = split < lens
+        first_g = starts + split
+        fk = keys[first_g[has_rest]]
+        assert np.all((fk > kk) | ((fk == kk) & (first_g[has_rest] > g_k)))

@@ -373,6 +373,30 @@ def measure_sorted_runs(tk, wl, torch, ctx):
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3), "kmin": kmin, "kmax": kmax,
                      "k": int(out[4].cpu().view(torch.int64)[0])}
+    # bulk deleteMin* (Section 5): consecutive pops from cursors at 0
+    d_cur = torch.zeros(1024, dtype=torch.uint64, device="cuda")
+    for name, kmin, kmax in (("delete_min_k65536", 1 << 16, None), ("delete_min_flex_k65536", 1 << 16,
+                                                                    (1 << 16) + (1 << 16) // 10)):
+        def pop():
+            if kmax is None:
+                return tk.topk_runs_delete_min(ctx, d_keys, d_off, d_cur, kmin, check=False)
+            return tk.topk_runs_delete_min_flexible(ctx, d_keys, d_off, d_cur, kmin, kmax, check=False)
+        d_cur.zero_()
+        for _ in range(2):
+            pop()
+        d_cur.zero_()
+        torch.cuda.synchronize()
+        reps = 10
+        e0.record()
+        for _ in range(reps):
+            pop()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        deleted = int(d_cur.view(torch.int64).sum().item())
+        res[name] = {"ms_per_pop": ms, "pops": reps, "deleted": deleted,
+                     "deleted_per_s": deleted / (reps * ms / 1e3)}
+    res["workload"] += "; deleteMin* pops of 2^16 (and flexible [2^16, 1.1*2^16]) from empty cursors"
     res["status"] = ctx.sync()
     return res
 

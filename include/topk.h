@@ -179,6 +179,45 @@ topk_status topk_select_sorted_runs_flexible(topk_ctx *ctx, const void *d_keys,
                                              uint64_t *d_kth_pos, uint64_t *d_k,
                                              const topk_params *params, void *stream);
 
+/* Bulk deleteMin* of the bulk priority queue (Section 5): the queue is the
+ * p sorted runs, each with a cursor; the objects of run r before its cursor
+ * are already deleted.  One call deletes the k smallest remaining objects
+ * by multisequence selection over the suffixes (Appendix A, msSelect,
+ * every bracket starting at the cursor instead of 0) and advances the
+ * cursors past them.  The objects deleted by run r are
+ * d_keys[off[r] + old cursor .. off[r] + new cursor); they are the k
+ * smallest of what remained, ties ordered by (run, position).
+ *   Arguments as topk_select_sorted_runs, and
+ *   d_cursor   p uint64 (caller-owned device memory, read and written):
+ *              in, the cursor of each run (0 <= cursor <= run length, a
+ *              larger one is reported by topk_status_sync() as
+ *              TOPK_EINVAL); out, the cursor after the deletion.
+ *   k          1 <= k < 2^32; k above the objects that remain is reported by
+ *              topk_status_sync() as TOPK_EINVAL (cursors then undefined).
+ *   d_kth_key, d_kth_run, d_kth_pos  the largest object deleted: its key,
+ *              run and position inside the run.
+ * Deleting k1 and then k2 leaves the same cursors as deleting k1 + k2 at
+ * once.  Insertion (Section 5's insert*) is the caller's: a run appended to
+ * d_keys with its offset and a zero cursor joins the queue. */
+topk_status topk_runs_delete_min(topk_ctx *ctx, const void *d_keys, const uint64_t *d_run_off,
+                                 uint32_t p, uint64_t *d_cursor, uint64_t k, topk_dtype dtype,
+                                 void *d_kth_key, uint32_t *d_kth_run, uint64_t *d_kth_pos,
+                                 const topk_params *params, void *stream);
+
+/* Flexible bulk deleteMin* (Section 5 with Section 4.3): deletes the k
+ * smallest remaining objects for some kmin <= k <= kmax found by the
+ * amsSelect search of topk_select_sorted_runs_flexible, writes that k to
+ * d_k (1 uint64, caller-owned device memory) and advances the cursors as
+ * topk_runs_delete_min does.  kmax above the objects that remain is
+ * clamped to them; kmin above them is reported as TOPK_EINVAL. */
+topk_status topk_runs_delete_min_flexible(topk_ctx *ctx, const void *d_keys,
+                                          const uint64_t *d_run_off, uint32_t p,
+                                          uint64_t *d_cursor, uint64_t kmin, uint64_t kmax,
+                                          topk_dtype dtype, void *d_kth_key,
+                                          uint32_t *d_kth_run, uint64_t *d_kth_pos,
+                                          uint64_t *d_k, const topk_params *params,
+                                          void *stream);
+
 /* Many independent selections in one persistent launch (no counterpart in the
  * paper: it is the selection of Section 2 run once per row).
  *   d_keys     all rows back to back, `dtype`.

@@ -53,6 +53,8 @@ class Oracle:
         lib.oracle_select.restype = i32
         lib.oracle_select_runs.argtypes = [vp, vp, u32, u64, vp, vp, vp]
         lib.oracle_select_runs.restype = i32
+        lib.oracle_runs_delete_min.argtypes = [vp, vp, u32, vp, u64, vp, vp]
+        lib.oracle_runs_delete_min.restype = i32
         lib.oracle_select_batched.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp]
         lib.oracle_select_batched.restype = i32
         self.lib = lib
@@ -92,6 +94,20 @@ class Oracle:
                                        _ptr(kr), _ptr(kp)) != 0:
             raise ValueError("oracle_select_runs rejected its arguments")
         return split, int(kr[0]), int(kp[0])
+
+    def runs_delete_min(self, keys: np.ndarray, run_off: np.ndarray, cursor: np.ndarray, k: int):
+        """(new cursor[p], kth_run, kth_pos) after deleting the k smallest
+        objects at or after the cursors (Section 5, deleteMin*)."""
+        a = _bits(keys, "u64")
+        off = np.ascontiguousarray(run_off, dtype=np.uint64)
+        p = off.size - 1
+        cur = np.array(cursor, dtype=np.uint64, copy=True)
+        kr = np.zeros(1, np.uint32)
+        kp = np.zeros(1, np.uint64)
+        if self.lib.oracle_runs_delete_min(_ptr(a), _ptr(off), p, _ptr(cur), int(k), _ptr(kr),
+                                           _ptr(kp)) != 0:
+            raise ValueError("oracle_runs_delete_min rejected its arguments")
+        return cur, int(kr[0]), int(kp[0])
 
     def select_batched(self, keys: np.ndarray, row_off: np.ndarray, row_k: np.ndarray,
                        dtype: str):
@@ -135,6 +151,10 @@ def select(keys, dtype, k):
 
 def select_runs(keys, run_off, k):
     return default().select_runs(keys, run_off, k)
+
+
+def runs_delete_min(keys, run_off, cursor, k):
+    return default().runs_delete_min(keys, run_off, cursor, k)
 
 
 def select_batched(keys, row_off, row_k, dtype):

@@ -221,6 +221,55 @@ int oracle_select_runs(const uint64_t *keys, const uint64_t *run_off, uint32_t p
     return 0;
 }
 
+int oracle_runs_delete_min(const uint64_t *keys, const uint64_t *run_off, uint32_t p,
+                           uint64_t *cursor, uint64_t k, uint32_t *kth_run,
+                           uint64_t *kth_pos)
+{
+    uint64_t remain = 0, i, j, len;
+    uint32_t r;
+    orc_pair *v;
+    orc_cmp_fn cmp = pair_cmp_for(ORC_U64);
+    if (!keys || !run_off || !cursor || !kth_run || !kth_pos || p == 0)
+        return -1;
+    if (run_off[0] != 0 || run_off[p] > 0xffffffffull)
+        return -1;
+    for (r = 0; r < p; ++r) {
+        if (run_off[r + 1] < run_off[r])
+            return -1;
+        len = run_off[r + 1] - run_off[r];
+        if (cursor[r] > len)
+            return -1;
+        remain += len - cursor[r];
+    }
+    if (k < 1 || k > remain)
+        return -1;
+    /* The queue's content: every pair at or after its run's cursor (room
+     * for all run_off[p] pairs, j of them filled). */
+    v = (orc_pair *)malloc((run_off[p] ? run_off[p] : 1) * sizeof(orc_pair));
+    if (!v)
+        return -1;
+    j = 0;
+    for (r = 0; r < p; ++r)
+        for (i = run_off[r] + cursor[r]; i < run_off[r + 1]; ++i) {
+            v[j].key = keys[i];
+            v[j].idx = i;
+            ++j;
+        }
+    qsort(v, (size_t)j, sizeof(orc_pair), cmp);
+    /* deleteMin*: the k smallest leave the queue, each run's cursor moving
+     * past those of its own. */
+    for (i = 0; i < k; ++i) {
+        r = run_holding(run_off, p, v[i].idx);
+        cursor[r] += 1;
+        if (i == k - 1) {
+            *kth_run = r;
+            *kth_pos = v[i].idx - run_off[r];
+        }
+    }
+    free(v);
+    return 0;
+}
+
 int oracle_select_batched(const void *keys, const uint64_t *row_off,
                           const uint32_t *row_k, uint32_t rows, int dtype,
                           const uint64_t *out_off, uint32_t *sel_idx,

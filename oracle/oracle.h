@@ -67,6 +67,19 @@ int oracle_select_runs(const uint64_t *keys, const uint64_t *run_off, uint32_t p
                        uint64_t k, uint64_t *split, uint32_t *kth_run,
                        uint64_t *kth_pos);
 
+/* Bulk deleteMin* (Section 5) of a priority queue held as p runs with
+ * cursors: the queue holds the pairs of run r at positions >= cursor[r].
+ * The k smallest of them, ordered as in oracle_select_runs, are deleted:
+ * cursor[r] (in/out) grows by the number of them in run r; *kth_run and
+ * *kth_pos receive the largest pair deleted.  The runs need not be sorted
+ * for this definition; when they are, the deleted pairs of run r are
+ * positions old cursor .. new cursor - 1.  Needs 1 <= k <= remaining,
+ * cursor[r] <= run length, total < 2^32.  Returns 0 or -1 (cursor untouched
+ * on -1). */
+int oracle_runs_delete_min(const uint64_t *keys, const uint64_t *run_off, uint32_t p,
+                           uint64_t *cursor, uint64_t k, uint32_t *kth_run,
+                           uint64_t *kth_pos);
+
 /* Independent selections over `rows` rows stored back to back:
  * row i is keys[row_off[i] .. row_off[i+1]) with its own k = row_k[i].
  * The selected indices (row-local, ascending pair order) of row i go to

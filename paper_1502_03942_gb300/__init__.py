@@ -91,6 +91,11 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_sorted_runs_flexible"):
         lib.topk_select_sorted_runs_flexible.argtypes = [vp, vp, vp, u32, u64, u64, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_sorted_runs_flexible.restype = st
+    if hasattr(lib, "topk_runs_delete_min"):
+        lib.topk_runs_delete_min.argtypes = [vp, vp, vp, u32, vp, u64, i32, vp, vp, vp, vp, vp]
+        lib.topk_runs_delete_min.restype = st
+        lib.topk_runs_delete_min_flexible.argtypes = [vp, vp, vp, u32, vp, u64, u64, i32, vp, vp, vp, vp, vp, vp]
+        lib.topk_runs_delete_min_flexible.restype = st
     if hasattr(lib, "topk_select_batched"):
         lib.topk_select_batched.argtypes = [vp, vp, vp, vp, u32, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_batched.restype = st
@@ -306,6 +311,62 @@ def topk_select_sorted_runs_flexible(ctx: Context, keys, run_off, kmin: int, kma
     _check(st, "topk_select_sorted_runs_flexible")
     if check:
         _check(ctx.sync(stream), "topk_select_sorted_runs_flexible (device)")
+    return out
+
+
+def topk_runs_delete_min(ctx: Context, keys, run_off, cursor, k: int, params: topk_params | None = None,
+                         stream=None, out=None, check: bool = True):
+    """Bulk deleteMin* over a queue of p sorted runs with cursors (Section 5):
+    deletes the k smallest objects after the cursors and advances ``cursor``
+    (p uint64 CUDA tensor, updated in place) past them.
+
+    Returns (kth_key[1] uint64, kth_run[1] uint32, kth_pos[1] uint64): the
+    largest object deleted."""
+    torch = _torch()
+    if keys.dtype != torch.uint64 or run_off.dtype != torch.uint64 or cursor.dtype != torch.uint64:
+        raise TypeError("keys, run_off and cursor must be uint64 tensors")
+    p = run_off.numel() - 1
+    if cursor.numel() != p:
+        raise ValueError("cursor needs one entry per run")
+    if out is None:
+        out = (torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device))
+    kk, kr, kp = out
+    st = load_library().topk_runs_delete_min(
+        ctx.handle, _ptr(keys), _ptr(run_off), p, _ptr(cursor), int(k), TOPK_U64, _ptr(kk), _ptr(kr), _ptr(kp),
+        ctypes.byref(params) if params is not None else None, _stream_ptr(stream))
+    _check(st, "topk_runs_delete_min")
+    if check:
+        _check(ctx.sync(stream), "topk_runs_delete_min (device)")
+    return out
+
+
+def topk_runs_delete_min_flexible(ctx: Context, keys, run_off, cursor, kmin: int, kmax: int,
+                                  params: topk_params | None = None, stream=None, out=None, check: bool = True):
+    """Flexible bulk deleteMin*: deletes the k smallest remaining objects for
+    some k in [kmin, kmax] and advances ``cursor`` in place.
+
+    Returns (kth_key[1], kth_run[1], kth_pos[1], k[1] uint64)."""
+    torch = _torch()
+    if keys.dtype != torch.uint64 or run_off.dtype != torch.uint64 or cursor.dtype != torch.uint64:
+        raise TypeError("keys, run_off and cursor must be uint64 tensors")
+    p = run_off.numel() - 1
+    if cursor.numel() != p:
+        raise ValueError("cursor needs one entry per run")
+    if out is None:
+        out = (torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device),
+               torch.empty(1, dtype=torch.uint64, device=keys.device))
+    kk, kr, kp, kout = out
+    st = load_library().topk_runs_delete_min_flexible(
+        ctx.handle, _ptr(keys), _ptr(run_off), p, _ptr(cursor), int(kmin), int(kmax), TOPK_U64, _ptr(kk),
+        _ptr(kr), _ptr(kp), _ptr(kout), ctypes.byref(params) if params is not None else None,
+        _stream_ptr(stream))
+    _check(st, "topk_runs_delete_min_flexible")
+    if check:
+        _check(ctx.sync(stream), "topk_runs_delete_min_flexible (device)")
     return out
 
 

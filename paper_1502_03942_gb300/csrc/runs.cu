@@ -70,6 +70,9 @@ struct RunsArgs {
     u64* kth_key;   // 1 (caller)
     u32* kth_run;
     u64* kth_pos;
+    // bulk priority queue (Section 5): run r starts at its cursor start[r]
+    // (objects before it were deleted); nullptr = every run from 0
+    const u64* start;
     // flexible k (Section 4.3, Algorithm amsSelect): any k in [kmin, kmax]
     u32 flexible;
     u64 kmin, kmax;
@@ -400,15 +403,19 @@ __global__ void __launch_bounds__(RUN_FIN_NT) k_runs_init(RunsArgs a) {
     for (u32 r = threadIdx.x; r < a.p; r += blockDim.x) {
         const u64 s = a.off[r], e = a.off[r + 1];
         const u64 len = e >= s ? e - s : 0;
-        a.lo[r] = 0;
+        const u64 c = a.start ? a.start[r] : 0;
         const u64 kcap = a.flexible ? a.kmax : a.k;
-        a.hi[r] = len < kcap ? len : kcap; // only the first k of a run can be selected
-        if (e < s) runs_latch(a, ST_EINVAL);
+        a.lo[r] = c < len ? c : len;
+        // only the first k after the start of a run can be selected
+        a.hi[r] = len - a.lo[r] < kcap ? len : a.lo[r] + kcap;
+        if (e < s || c > len) runs_latch(a, ST_EINVAL);
     }
     __syncthreads();
     const u64 m = block_prefix_brackets(a, sm.warp_sums, &sm.carry);
     if (threadIdx.x == 0) {
         st->m = m;
+        // (m holds every remaining object when fewer than k remain in total)
+        if ((a.flexible ? a.kmin : a.k) > m && st->phase == RPH_RUN) runs_latch(a, ST_EINVAL);
         if (a.flexible && st->kmax > m) st->kmax = m;
         if (st->phase == RPH_RUN && m <= RUN_T) st->phase = RPH_FINISH;
     }
@@ -602,7 +609,8 @@ namespace topk {
 static topk_status run_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off, uint32_t p,
                                    uint64_t k, bool flexible, uint64_t kmin, uint64_t kmax, topk_dtype dtype,
                                    uint64_t* d_split, void* d_kth_key, uint32_t* d_kth_run, uint64_t* d_kth_pos,
-                                   uint64_t* d_k, const topk_params* params, void* stream) {
+                                   uint64_t* d_k, const topk_params* params, void* stream,
+                                   const uint64_t* d_start = nullptr) {
     if (!ctx || !d_keys || !d_run_off || !d_split || !d_kth_key || !d_kth_run || !d_kth_pos) return TOPK_EINVAL;
     if (flexible && (!d_k || kmin == 0 || kmin > kmax || kmax > 0xFFFFFFFFull)) return TOPK_EINVAL;
     if (!flexible && (k == 0 || k > 0xFFFFFFFFull)) return TOPK_EINVAL;
@@ -621,6 +629,7 @@ static topk_status run_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint
     a.kmin = kmin;
     a.kmax = kmax;
     a.k_out = flexible ? d_k : nullptr;
+    a.start = d_start;
     a.d = prm.sample_size ? std::min<u32>(std::max<u32>(prm.sample_size, 1), RUN_MAX_D) : 64;
     a.seed = prm.seed ? prm.seed : 0x13198A2E03707344ull;
     a.flags = prm.flags;
@@ -689,4 +698,23 @@ extern "C" topk_status topk_select_sorted_runs_flexible(topk_ctx* ctx, const voi
                                                         void* stream) {
     return run_sorted_runs(ctx, d_keys, d_run_off, p, 0, true, kmin, kmax, dtype, d_split, d_kth_key, d_kth_run,
                            d_kth_pos, d_k, params, stream);
+}
+
+extern "C" topk_status topk_runs_delete_min(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off, uint32_t p,
+                                            uint64_t* d_cursor, uint64_t k, topk_dtype dtype, void* d_kth_key,
+                                            uint32_t* d_kth_run, uint64_t* d_kth_pos, const topk_params* params,
+                                            void* stream) {
+    if (!d_cursor) return TOPK_EINVAL;
+    return run_sorted_runs(ctx, d_keys, d_run_off, p, k, false, 0, 0, dtype, d_cursor, d_kth_key, d_kth_run,
+                           d_kth_pos, nullptr, params, stream, d_cursor);
+}
+
+extern "C" topk_status topk_runs_delete_min_flexible(topk_ctx* ctx, const void* d_keys, const uint64_t* d_run_off,
+                                                     uint32_t p, uint64_t* d_cursor, uint64_t kmin, uint64_t kmax,
+                                                     topk_dtype dtype, void* d_kth_key, uint32_t* d_kth_run,
+                                                     uint64_t* d_kth_pos, uint64_t* d_k, const topk_params* params,
+                                                     void* stream) {
+    if (!d_cursor) return TOPK_EINVAL;
+    return run_sorted_runs(ctx, d_keys, d_run_off, p, 0, true, kmin, kmax, dtype, d_cursor, d_kth_key, d_kth_run,
+                           d_kth_pos, d_k, params, stream, d_cursor);
 }

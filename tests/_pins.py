@@ -241,6 +241,41 @@ def check_runs_vs_merge(orc, seed=3):
     return fails
 
 
+def check_delete_min_vs_heap(orc, seed=5):
+    """Bulk deleteMin* (Section 5) against a textbook binary-heap priority
+    queue (heapq): the queue holds (key, run, position) of every object at or
+    after its run's cursor; k pops give the deleted objects.  Sequences of
+    bulk deletions from random cursors down to an empty queue."""
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for trial in range(30):
+        p = int(g.integers(1, 7))
+        lens = g.integers(0, 10, size=p)
+        if lens.sum() == 0:
+            lens[0] = 1
+        off = np.zeros(p + 1, np.uint64)
+        off[1:] = np.cumsum(lens)
+        keys = (g.integers(0, 4, size=int(off[-1])) * 5).astype(np.uint64)
+        for r in range(p):
+            keys[int(off[r]):int(off[r + 1])].sort()
+        cursor = np.array([int(g.integers(0, l + 1)) for l in lens], np.uint64)
+        heap = []
+        for r in range(p):
+            for j in range(int(cursor[r]), int(lens[r])):
+                heapq.heappush(heap, (int(keys[int(off[r]) + j]), r, j))
+        while heap:
+            k = int(g.integers(1, len(heap) + 1))
+            popped = [heapq.heappop(heap) for _ in range(k)]
+            want = cursor.copy()
+            for _, r, _j in popped:
+                want[r] += 1
+            cursor, kr, kp = orc.runs_delete_min(keys, off, cursor, k)
+            if list(cursor) != list(want) or (kr, kp) != popped[-1][1:]:
+                fails.append(f"deleteMin* vs heapq trial={trial} k={k}")
+                return fails
+    return fails
+
+
 def check_batched_rows(orc, seed=4):
     fails = []
     g = np.random.Generator(np.random.Philox(seed))
@@ -261,4 +296,4 @@ def check_batched_rows(orc, seed=4):
 
 ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_cases,
               check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
-              check_batched_rows]
+              check_batched_rows, check_delete_min_vs_heap]

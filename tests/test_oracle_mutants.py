@@ -27,6 +27,8 @@ MUTATIONS = {
                        "*kth_idx = (uint32_t)v[k > 1 ? k - 2 : 0].idx;"),
     "runs_pos_off_by_one": ("*kth_pos = g - run_off[r];", "*kth_pos = g - run_off[r] + 1;"),
     "runs_bisection_strict": ("if (run_off[mid] <= g)", "if (run_off[mid] < g)"),
+    "delete_ignores_cursor": ("for (i = run_off[r] + cursor[r]; i < run_off[r + 1]; ++i) {",
+                              "for (i = run_off[r]; i < run_off[r + 1]; ++i) {"),
     "take_k_minus_one": ("for (i = 0; i < k; ++i)             /* ranks 1..k */",
                          "for (i = 1; i < k; ++i)             /* ranks 1..k */"),
 }

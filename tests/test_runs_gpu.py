@@ -192,3 +192,124 @@ def test_flexible_full_configuration(tk, ctx):
         first_g = starts + split
         fk = keys[first_g[has_rest]]
         assert np.all((fk > kk) | ((fk == kk) & (first_g[has_rest] > g_k)))
+
+
+# ---- bulk deleteMin* over sorted runs with cursors (Section 5) ----
+
+def pop_and_check(tk, ctx, keys, off, d_keys, d_off, d_cur, cursor, k, params=None):
+    kk, kr, kp = tk.topk_runs_delete_min(ctx, d_keys, d_off, d_cur, k, params=params)
+    want, wr, wp = oracle.runs_delete_min(keys, off, cursor, k)
+    assert np.array_equal(bits_of(d_cur), want), "cursors differ"
+    assert (int(bits_of(kr)[0]), int(bits_of(kp)[0])) == (wr, wp), "largest deleted object differs"
+    assert int(bits_of(kk)[0]) == int(keys[int(off[wr]) + wp])
+    return want
+
+
+@pytest.mark.parametrize("p,maxlen,alphabet", [(1, 20000, None), (5, 3000, 3), (64, 2000, None),
+                                               (700, 400, 20), (1024, 3000, None)])
+def test_delete_min_sequence(tk, ctx, p, maxlen, alphabet):
+    """Pops of random sizes from empty cursors until the queue is empty; each
+    pop against the oracle's deleteMin*."""
+    keys, off = make_runs(p, maxlen, seed=101 + p, alphabet=alphabet)
+    total = int(off[-1])
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    cursor = np.zeros(p, np.uint64)
+    d_cur = to_device(cursor, "u64")
+    g = np.random.Generator(np.random.Philox(p))
+    left = total
+    sizes = [1, 2, 1000]
+    while left > 0:
+        k = sizes.pop(0) if sizes else int(g.integers(1, max(2, total // 5)))
+        k = min(k, left)
+        cursor = pop_and_check(tk, ctx, keys, off, d_keys, d_off, d_cur, cursor, k)
+        left -= k
+    assert np.array_equal(cursor, np.diff(off))
+
+
+def test_delete_min_from_given_cursors(tk, ctx):
+    """Arbitrary starting cursors, some at 0, some at the run's end; the
+    composition of two pops equals one pop of their sum."""
+    keys, off = make_runs(300, 2000, seed=111, alphabet=50)
+    lens = np.diff(off)
+    g = np.random.Generator(np.random.Philox(7))
+    cursor = np.array([int(g.integers(0, l + 1)) for l in lens], np.uint64)
+    cursor[:10] = 0
+    cursor[10:20] = lens[10:20]
+    remain = int((lens - cursor).sum())
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    for k1, k2 in ((1, 1), (remain // 3, remain // 5), (remain - 1, 1)):
+        d_cur = to_device(cursor, "u64")
+        c1 = pop_and_check(tk, ctx, keys, off, d_keys, d_off, d_cur, cursor, k1)
+        c2 = pop_and_check(tk, ctx, keys, off, d_keys, d_off, d_cur, c1, k2)
+        d_once = to_device(cursor, "u64")
+        tk.topk_runs_delete_min(ctx, d_keys, d_off, d_once, k1 + k2)
+        assert np.array_equal(bits_of(d_once), c2)
+
+
+def test_delete_min_rejects(tk, ctx):
+    keys, off = make_runs(8, 100, seed=112)
+    lens = np.diff(off)
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    cursor = lens.copy()
+    cursor[0] = 0
+    with pytest.raises(tk.TopkError) as e:  # more than remain
+        tk.topk_runs_delete_min(ctx, d_keys, d_off, to_device(cursor, "u64"), int(lens[0]) + 1)
+    assert e.value.status == tk.TOPK_EINVAL
+    bad = np.zeros(8, np.uint64)
+    bad[3] = lens[3] + 1  # cursor past its run
+    with pytest.raises(tk.TopkError) as e:
+        tk.topk_runs_delete_min(ctx, d_keys, d_off, to_device(bad, "u64"), 1)
+    assert e.value.status == tk.TOPK_EINVAL
+    # the context stays usable
+    d_cur = to_device(np.zeros(8, np.uint64), "u64")
+    pop_and_check(tk, ctx, keys, off, d_keys, d_off, d_cur, np.zeros(8, np.uint64), 5)
+
+
+def test_delete_min_flexible_sequence(tk, ctx):
+    """Flexible pops: each k in its range, the cursors those of the oracle's
+    deleteMin* for that k; clamped at the end of the queue."""
+    keys, off = make_runs(200, 5000, seed=113)
+    total = int(off[-1])
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    cursor = np.zeros(200, np.uint64)
+    d_cur = to_device(cursor, "u64")
+    left = total
+    step = total // 7
+    while left > 0:
+        kmin = min(step, left)
+        kmax = kmin + step // 8
+        kk, kr, kp, kout = tk.topk_runs_delete_min_flexible(ctx, d_keys, d_off, d_cur, kmin, kmax)
+        k = int(bits_of(kout)[0])
+        assert kmin <= k <= min(kmax, left)
+        want, wr, wp = oracle.runs_delete_min(keys, off, cursor, k)
+        assert np.array_equal(bits_of(d_cur), want)
+        assert (int(bits_of(kr)[0]), int(bits_of(kp)[0])) == (wr, wp)
+        cursor = want
+        left -= k
+    assert np.array_equal(cursor, np.diff(off))
+
+
+def test_delete_min_full_configuration(tk, ctx):
+    """1024 runs of 2^U(10,20) sorted u64 keys: three pops of 2^16 leave the
+    cursors of one selection of 3 * 2^16, and every run's last deleted
+    object is below the largest deleted, its first remaining one above."""
+    keys, off = wl.sorted_runs(1024, 10, 20, seed=3)
+    d_keys, d_off = to_device(keys, "u64"), to_device(off, "u64")
+    import torch
+    d_cur = torch.zeros(1024, dtype=torch.uint64, device="cuda")
+    for _ in range(3):
+        kk, kr, kp = tk.topk_runs_delete_min(ctx, d_keys, d_off, d_cur, 1 << 16)
+    split, _, _, _ = tk.topk_select_sorted_runs(ctx, d_keys, d_off, 3 << 16)
+    cur = bits_of(d_cur).astype(np.int64)
+    assert np.array_equal(cur, bits_of(split).astype(np.int64))
+    lens = np.diff(off).astype(np.int64)
+    starts = off[:-1].astype(np.int64)
+    kr, kp, kk = int(bits_of(kr)[0]), int(bits_of(kp)[0]), int(bits_of(kk)[0])
+    g_k = int(off[kr]) + kp
+    assert cur.sum() == 3 << 16 and kk == int(keys[g_k]) and cur[kr] == kp + 1
+    has = cur > 0
+    lk = keys[(starts + cur - 1)[has]]
+    assert np.all((lk < kk) | ((lk == kk) & ((starts + cur - 1)[has] <= g_k)))
+    rest = cur < lens
+    fk = keys[(starts + cur)[rest]]
+    assert np.all((fk > kk) | ((fk == kk) & ((starts + cur)[rest] > g_k)))

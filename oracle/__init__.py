@@ -8,8 +8,12 @@ The C file next to this one (``oracle.c``) states what is computed: all n pairs
 (key, position) sorted once under the key type's value order (integers by
 value, floats by IEEE 754 totalOrder), first k taken (paper, Section 2 for the
 (value, position) tie-break, Section 4 for the problem, Appendix A for the
-multisequence split positions).  This module only loads that library and moves
-numpy arrays in and out of it.
+multisequence split positions, Section 5 for deleteMin* over runs with
+cursors).  For the top-k most frequent objects (Section 7) it follows the
+algorithms' steps on one PE: Bernoulli sample decisions from Philox4x32-10
+(written from its published definition), counting by sort-and-run-length,
+the k (PAC) or k* (EC, then an exact recount) most frequent.  This module
+only loads that library and moves numpy arrays in and out of it.
 """
 from __future__ import annotations
 
@@ -55,6 +59,16 @@ class Oracle:
         lib.oracle_select_runs.restype = i32
         lib.oracle_runs_delete_min.argtypes = [vp, vp, u32, vp, u64, vp, vp]
         lib.oracle_runs_delete_min.restype = i32
+        lib.oracle_philox4x32_10.argtypes = [vp, vp, vp]
+        lib.oracle_philox4x32_10.restype = None
+        lib.oracle_sample_threshold.argtypes = [ctypes.c_double]
+        lib.oracle_sample_threshold.restype = u64
+        lib.oracle_bernoulli_sample.argtypes = [u64, u64, u64, vp]
+        lib.oracle_bernoulli_sample.restype = i32
+        lib.oracle_frequent.argtypes = [vp, u64, vp, u32, u32, i32, vp, vp, vp]
+        lib.oracle_frequent.restype = i32
+        lib.oracle_frequent_plan.argtypes = [u64, u32, ctypes.c_double, ctypes.c_double, u32, i32, vp, vp]
+        lib.oracle_frequent_plan.restype = i32
         lib.oracle_select_batched.argtypes = [vp, vp, vp, u32, i32, vp, vp, vp]
         lib.oracle_select_batched.restype = i32
         self.lib = lib
@@ -109,6 +123,50 @@ class Oracle:
             raise ValueError("oracle_runs_delete_min rejected its arguments")
         return cur, int(kr[0]), int(kp[0])
 
+    # ---- top-k most frequent objects (Section 7) ----
+
+    def philox(self, ctr, key):
+        c = np.ascontiguousarray(ctr, dtype=np.uint32)
+        kk = np.ascontiguousarray(key, dtype=np.uint32)
+        out = np.zeros(4, np.uint32)
+        self.lib.oracle_philox4x32_10(_ptr(c), _ptr(kk), _ptr(out))
+        return out
+
+    def sample_threshold(self, rho: float) -> int:
+        return int(self.lib.oracle_sample_threshold(float(rho)))
+
+    def bernoulli_sample(self, n: int, seed: int, threshold: int) -> np.ndarray:
+        """mask[n] uint8: 1 where element i is sampled (Section 7.1)."""
+        mask = np.zeros(max(n, 1), np.uint8)
+        if self.lib.oracle_bernoulli_sample(int(n), int(seed), int(threshold), _ptr(mask)) != 0:
+            raise ValueError("oracle_bernoulli_sample rejected its arguments")
+        return mask[:n]
+
+    def frequent(self, objects: np.ndarray, mask: np.ndarray, k: int, kstar: int = 0,
+                 exact: bool = False):
+        """(objects[k], counts[k], sample_size): Algorithm PAC (sample counts)
+        or EC (exact counts of the k most frequent of k* candidates), most
+        frequent first, equal counts by the smaller object."""
+        obj = np.ascontiguousarray(objects, dtype=np.uint32)
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        out_obj = np.zeros(k, np.uint32)
+        out_cnt = np.zeros(k, np.uint64)
+        ss = np.zeros(1, np.uint64)
+        if self.lib.oracle_frequent(_ptr(obj), obj.size, _ptr(m), int(k), int(kstar), int(bool(exact)),
+                                    _ptr(out_obj), _ptr(out_cnt), _ptr(ss)) != 0:
+            raise ValueError("oracle_frequent rejected its arguments")
+        return out_obj, out_cnt, int(ss[0])
+
+    def frequent_plan(self, n: int, k: int, eps: float, delta: float, pes: int = 1,
+                      exact: bool = False):
+        """(rho, kstar) from the accuracy targets (Sections 7.1, 7.2)."""
+        rho = np.zeros(1, np.float64)
+        ks = np.zeros(1, np.uint32)
+        if self.lib.oracle_frequent_plan(int(n), int(k), float(eps), float(delta), int(pes),
+                                         int(bool(exact)), _ptr(rho), _ptr(ks)) != 0:
+            raise ValueError("oracle_frequent_plan rejected its arguments")
+        return float(rho[0]), int(ks[0])
+
     def select_batched(self, keys: np.ndarray, row_off: np.ndarray, row_k: np.ndarray,
                        dtype: str):
         """(sel_idx concatenated per row, out_off, kth_idx[rows]); indices row-local."""
@@ -159,3 +217,19 @@ def runs_delete_min(keys, run_off, cursor, k):
 
 def select_batched(keys, row_off, row_k, dtype):
     return default().select_batched(keys, row_off, row_k, dtype)
+
+
+def bernoulli_sample(n, seed, threshold):
+    return default().bernoulli_sample(n, seed, threshold)
+
+
+def sample_threshold(rho):
+    return default().sample_threshold(rho)
+
+
+def frequent(objects, mask, k, kstar=0, exact=False):
+    return default().frequent(objects, mask, k, kstar, exact)
+
+
+def frequent_plan(n, k, eps, delta, pes=1, exact=False):
+    return default().frequent_plan(n, k, eps, delta, pes, exact)

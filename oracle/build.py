@@ -17,7 +17,7 @@ CFLAGS = ["-O2", "-std=c99", "-Wall", "-Wextra", "-fPIC", "-shared"]
 def compile_source(src: str, out: str) -> str:
     """gcc one oracle source file into a shared library at ``out``."""
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.run(["gcc", *CFLAGS, "-I", HERE, src, "-o", tmp], check=True)
+    subprocess.run(["gcc", *CFLAGS, "-I", HERE, src, "-o", tmp, "-lm"], check=True)
     os.replace(tmp, out)
     return out
 

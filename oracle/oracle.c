@@ -16,6 +16,7 @@
  */
 #include "oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -288,5 +289,209 @@ int oracle_select_batched(const void *keys, const uint64_t *row_off,
                           kth_idx + i) != 0)
             return -1;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Top-k most frequent objects (Section 7).
+ * ------------------------------------------------------------------------ */
+
+/* Philox4x32-10 from its published definition (Salmon, Moraes, Dror, Shaw,
+ * SC'11): ten rounds of two 32x32->64 multiplications whose halves are
+ * permuted and xor-ed with the counter words and the round key; the key
+ * grows by the Weyl constants between rounds. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    int round;
+    for (round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0;
+        c1 = lo1;
+        c2 = hi0 ^ c3 ^ k1;
+        c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+}
+
+uint64_t oracle_sample_threshold(double rho)
+{
+    if (!(rho > 0.0))
+        return 0;
+    if (rho >= 1.0)
+        return (uint64_t)1 << 32;
+    return (uint64_t)floor(ldexp(rho, 32));
+}
+
+int oracle_bernoulli_sample(uint64_t n, uint64_t seed, uint64_t threshold, uint8_t *mask)
+{
+    uint64_t i;
+    uint32_t ctr[4], key[2], out[4];
+    if (!mask && n)
+        return -1;
+    key[0] = (uint32_t)seed;
+    key[1] = (uint32_t)(seed >> 32);
+    for (i = 0; i < n; ++i) {
+        uint64_t j = i / 4;
+        if (i % 4 == 0) {
+            ctr[0] = (uint32_t)j;
+            ctr[1] = (uint32_t)(j >> 32);
+            ctr[2] = ORACLE_SAMPLE_STREAM;
+            ctr[3] = 0;
+            oracle_philox4x32_10(ctr, key, out);
+        }
+        mask[i] = (uint64_t)out[i % 4] < threshold ? 1 : 0;
+    }
+    return 0;
+}
+
+typedef struct {
+    uint32_t obj;
+    uint64_t count;
+} orc_freq;
+
+static int cmp_u32(const void *pa, const void *pb)
+{
+    uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
+    return a < b ? -1 : a > b ? 1 : 0;
+}
+
+/* More frequent first; equal counts by the smaller object. */
+static int cmp_freq(const void *pa, const void *pb)
+{
+    const orc_freq *x = (const orc_freq *)pa, *y = (const orc_freq *)pb;
+    if (x->count != y->count)
+        return x->count > y->count ? -1 : 1;
+    return x->obj < y->obj ? -1 : x->obj > y->obj ? 1 : 0;
+}
+
+/* Sorts `m` objects and counts runs of equal ones; returns the number of
+ * distinct objects written to `out` (room for m). */
+static uint64_t count_objects(uint32_t *objs, uint64_t m, orc_freq *out)
+{
+    uint64_t i, d = 0;
+    qsort(objs, (size_t)m, sizeof(uint32_t), cmp_u32);
+    for (i = 0; i < m; ++i) {
+        if (d > 0 && out[d - 1].obj == objs[i]) {
+            out[d - 1].count += 1;
+        } else {
+            out[d].obj = objs[i];
+            out[d].count = 1;
+            ++d;
+        }
+    }
+    return d;
+}
+
+int oracle_frequent(const uint32_t *obj, uint64_t n, const uint8_t *mask, uint32_t k,
+                    uint32_t kstar, int exact, uint32_t *out_obj, uint64_t *out_cnt,
+                    uint64_t *sample_size)
+{
+    uint64_t i, m = 0, d;
+    uint32_t *sample, *cand;
+    orc_freq *freq;
+    if (!obj || !mask || !out_obj || !out_cnt || k == 0 || n == 0)
+        return -1;
+    if (exact && kstar < k)
+        return -1;
+    /* Step 1: the Bernoulli sample (the decisions are given). */
+    sample = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    freq = (orc_freq *)malloc((size_t)n * sizeof(orc_freq));
+    if (!sample || !freq) {
+        free(sample);
+        free(freq);
+        return -1;
+    }
+    for (i = 0; i < n; ++i)
+        if (mask[i])
+            sample[m++] = obj[i];
+    if (sample_size)
+        *sample_size = m;
+    /* Step 2: count the sampled objects. */
+    d = count_objects(sample, m, freq);
+    /* Step 3: the most frequently sampled ones (k for PAC, k* for EC). */
+    qsort(freq, (size_t)d, sizeof(orc_freq), cmp_freq);
+    if (!exact) {
+        if (k > d) {
+            free(sample);
+            free(freq);
+            return -1;
+        }
+        for (i = 0; i < k; ++i) {
+            out_obj[i] = freq[i].obj;
+            out_cnt[i] = freq[i].count;
+        }
+        free(sample);
+        free(freq);
+        return 0;
+    }
+    if (kstar > d) {
+        free(sample);
+        free(freq);
+        return -1;
+    }
+    /* Step 4 (EC): count the k* candidates exactly over the whole input. */
+    cand = sample; /* reuse: the k* candidate objects, sorted */
+    for (i = 0; i < kstar; ++i)
+        cand[i] = freq[i].obj;
+    qsort(cand, kstar, sizeof(uint32_t), cmp_u32);
+    for (i = 0; i < kstar; ++i) {
+        freq[i].obj = cand[i];
+        freq[i].count = 0;
+    }
+    for (i = 0; i < n; ++i) {
+        uint32_t lo = 0, hi = kstar; /* binary search among the candidates */
+        while (lo < hi) {
+            uint32_t mid = lo + (hi - lo) / 2;
+            if (cand[mid] < obj[i])
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo < kstar && cand[lo] == obj[i])
+            freq[lo].count += 1;
+    }
+    /* Step 5: the k most frequent candidates by exact count. */
+    qsort(freq, kstar, sizeof(orc_freq), cmp_freq);
+    for (i = 0; i < k; ++i) {
+        out_obj[i] = freq[i].obj;
+        out_cnt[i] = freq[i].count;
+    }
+    free(sample);
+    free(freq);
+    return 0;
+}
+
+int oracle_frequent_plan(uint64_t n, uint32_t k, double eps, double delta, uint32_t pes,
+                         int exact, double *rho, uint32_t *kstar)
+{
+    double rho_n, ks;
+    if (!rho || !kstar || n == 0 || k == 0 || !(eps > 0.0) || !(delta > 0.0) ||
+        !(delta < 1.0) || pes == 0)
+        return -1;
+    if (!exact) {
+        /* Equation sampleSize (Section 7.1). */
+        double a = 3.0 / k * log(4.0 * n / delta);
+        double b = 2.0 * log(2.0 * k / delta);
+        rho_n = 4.0 / (eps * eps) * (a > b ? a : b);
+        *kstar = k;
+    } else {
+        /* Section 7.2: k* = max(k, (1/eps) sqrt((2 log p / p) ln(n/delta))),
+         * sample size 2 ln(n/delta) / (eps^2 k*). */
+        ks = sqrt(2.0 * log2((double)pes) / pes * log(n / delta)) / eps;
+        ks = ceil(ks);
+        *kstar = ks > k ? (ks > 4294967295.0 ? 0xffffffffu : (uint32_t)ks) : k;
+        rho_n = 2.0 / (eps * eps * *kstar) * log(n / delta);
+    }
+    *rho = rho_n >= (double)n ? 1.0 : rho_n / n;
     return 0;
 }

@@ -90,6 +90,44 @@ int oracle_select_batched(const void *keys, const uint64_t *row_off,
                           const uint64_t *out_off, uint32_t *sel_idx,
                           uint32_t *kth_idx);
 
+/* ---- Top-k most frequent objects (Section 7) ---- */
+
+/* Philox4x32-10 (Salmon et al., SC'11): out = the four output words for
+ * counter ctr[0..3] and key key[0..1]. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+/* Counter word 2 of the sampling stream. */
+#define ORACLE_SAMPLE_STREAM 0x53414d50u
+
+/* Integer threshold of sampling probability rho: floor(rho * 2^32), 2^32
+ * for rho >= 1, 0 for rho <= 0. */
+uint64_t oracle_sample_threshold(double rho);
+
+/* Bernoulli sample decisions (Section 7.1): element i is sampled iff word
+ * i % 4 of Philox4x32-10 at counter (i / 4 low, i / 4 high,
+ * ORACLE_SAMPLE_STREAM, 0) and key (seed low, seed high) is below
+ * `threshold`.  mask[i] = 1 when sampled.  Returns 0 or -1. */
+int oracle_bernoulli_sample(uint64_t n, uint64_t seed, uint64_t threshold, uint8_t *mask);
+
+/* Algorithm PAC (exact = 0, Section 7.1) or EC (exact = 1, Section 7.2) on
+ * one PE, the sample given as mask: counts the sampled objects; PAC
+ * returns the k most frequently sampled objects with their sample counts;
+ * EC takes the k* most frequently sampled ones, counts them over the whole
+ * input and returns the k most frequent of them with their exact counts.
+ * "Most frequent" orders by count, larger first, then by the smaller
+ * object.  Output in that order.  *sample_size (may be NULL) receives the
+ * number of sampled elements.  Returns -1 when fewer than k (PAC) or k*
+ * (EC) distinct objects were sampled. */
+int oracle_frequent(const uint32_t *obj, uint64_t n, const uint8_t *mask, uint32_t k,
+                    uint32_t kstar, int exact, uint32_t *out_obj, uint64_t *out_cnt,
+                    uint64_t *sample_size);
+
+/* Sampling probability and k* from the accuracy targets: PAC by equation
+ * sampleSize (Section 7.1), EC by Section 7.2 (log p taken base 2).  rho is
+ * clamped to 1.  Returns 0 or -1. */
+int oracle_frequent_plan(uint64_t n, uint32_t k, double eps, double delta, uint32_t pes,
+                         int exact, double *rho, uint32_t *kstar);
+
 #ifdef __cplusplus
 }
 #endif

@@ -276,6 +276,150 @@ def check_delete_min_vs_heap(orc, seed=5):
     return fails
 
 
+# ---- top-k most frequent objects (Section 7) ----
+
+def load_kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def check_philox_kat(orc):
+    """The oracle's Philox4x32-10 against the published known-answer vectors."""
+    return [f"philox KAT {i}" for i, (c, k, want) in enumerate(load_kat())
+            if list(orc.philox(c, k)) != want]
+
+
+def load_pac_example():
+    ex = {"pes": []}
+    with open(os.path.join(GOLDEN, "pac_worked_example.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, val = line.split(":", 1)
+            if key.startswith("pe "):
+                ex["pes"].append("".join(val.split()))
+            elif key in ("rho",):
+                ex[key] = float(val)
+            elif key in ("k", "kstar"):
+                ex[key] = int(val)
+            else:
+                w = val.split()
+                ex[key] = [(w[i], int(w[i + 1])) for i in range(0, len(w), 2)]
+    return ex
+
+
+def check_pac_worked_example(orc):
+    """The paper's worked example: PAC's estimates (sample count / rho,
+    rounded), EC's candidates with their exact counts and EC's result."""
+    fails = []
+    ex = load_pac_example()
+    text = "".join(ex["pes"])
+    objects = np.array([ord(ch.upper()) for ch in text], np.uint32)
+    mask = np.array([1 if ch.islower() else 0 for ch in text], np.uint8)
+    name = lambda o: chr(int(o))
+    # sample counts of every sampled object (k = all distinct sampled)
+    d = len(ex["sample_counts"])
+    o, c, m = orc.frequent(objects, mask, d)
+    if sorted(zip(map(name, o), map(int, c))) != sorted(ex["sample_counts"]) or m != int(mask.sum()):
+        fails.append("worked example: sample counts")
+    o, c, _ = orc.frequent(objects, mask, ex["k"])
+    est = [(name(a), int(round(int(b) / ex["rho"]))) for a, b in zip(o, c)]
+    if sorted(est) != sorted(ex["pac_estimated"]):
+        fails.append(f"worked example: PAC estimates {est}")
+    o, c, _ = orc.frequent(objects, mask, ex["kstar"], kstar=ex["kstar"], exact=True)
+    if sorted(zip(map(name, o), map(int, c))) != sorted(ex["ec_candidates"]):
+        fails.append("worked example: EC candidates")
+    o, c, _ = orc.frequent(objects, mask, ex["k"], kstar=ex["kstar"], exact=True)
+    got = list(zip(map(name, o), map(int, c)))
+    if got != ex["ec_result"] or sorted(got) != sorted(ex["exact"]):
+        fails.append(f"worked example: EC result {got}")
+    return fails
+
+
+def check_frequent_vs_counter(orc, seed=6):
+    """PAC and EC against collections.Counter over the sampled (PAC) or all
+    (EC) objects, most frequent first, equal counts by the smaller object."""
+    import collections
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for trial in range(25):
+        n = int(g.integers(1, 3000))
+        objects = ((g.integers(0, int(g.integers(1, 60)), size=n).astype(np.uint64) * 2654435761)
+                   % (1 << 32)).astype(np.uint32)
+        mask = (g.random(n) < g.uniform(0.05, 1.0)).astype(np.uint8)
+        sampled = collections.Counter(int(x) for x, s in zip(objects, mask) if s)
+        ranked = sorted(sampled.items(), key=lambda t: (-t[1], t[0]))
+        if not ranked:
+            continue
+        k = int(g.integers(1, len(ranked) + 1))
+        o, c, _ = orc.frequent(objects, mask, k)
+        if list(zip(map(int, o), map(int, c))) != ranked[:k]:
+            fails.append(f"PAC vs Counter trial={trial}")
+            return fails
+        kstar = int(g.integers(k, len(ranked) + 1))
+        full = collections.Counter(int(x) for x in objects)
+        cand = sorted(((x, full[x]) for x, _ in ranked[:kstar]), key=lambda t: (-t[1], t[0]))
+        o, c, _ = orc.frequent(objects, mask, k, kstar=kstar, exact=True)
+        if list(zip(map(int, o), map(int, c))) != cand[:k]:
+            fails.append(f"EC vs Counter trial={trial}")
+            return fails
+    return fails
+
+
+def check_bernoulli_decisions(orc, seed=7):
+    """Element i is sampled iff word i % 4 of Philox at counter (i / 4, 0,
+    stream, 0) is below the threshold; the sampled fraction is within six
+    standard deviations of rho; rho = 1 samples everything, 0 nothing."""
+    fails = []
+    n = 1 << 16
+    for rho in (0.074, 0.5):
+        thr = orc.sample_threshold(rho)
+        if thr != int(rho * 2 ** 32):
+            fails.append(f"threshold {rho}")
+        mask = orc.bernoulli_sample(n, 0x1234_5678_9ABC_DEF0, thr)
+        frac = mask.mean()
+        if abs(frac - rho) > 6 * (rho * (1 - rho) / n) ** 0.5:
+            fails.append(f"sampled fraction {frac} for rho {rho}")
+        for i in (0, 1, 2, 3, 4, 7, 12345, n - 1):
+            j = i // 4
+            w = orc.philox([j & 0xFFFFFFFF, j >> 32, 0x53414D50, 0], [0x9ABCDEF0, 0x12345678])[i % 4]
+            if int(mask[i]) != int(int(w) < thr):
+                fails.append(f"decision of element {i}")
+    if orc.bernoulli_sample(1000, 5, orc.sample_threshold(1.0)).min() != 1:
+        fails.append("rho = 1")
+    if orc.bernoulli_sample(1000, 5, orc.sample_threshold(0.0)).max() != 0:
+        fails.append("rho = 0")
+    return fails
+
+
+def check_frequent_plan(orc):
+    """Sample sizes against the closed forms the paper states: PAC's
+    8 ln(2k/delta) / eps^2 where the second term of equation sampleSize
+    dominates, EC's 2 ln(n/delta) / (eps^2 k) with k* = k on one PE; rho
+    is clamped to 1."""
+    import math
+    fails = []
+    n, k, eps, delta = 1 << 40, 32, 3e-4, 1e-4
+    rho, ks = orc.frequent_plan(n, k, eps, delta)
+    if ks != k or abs(rho * n / (8 / eps ** 2 * math.log(2 * k / delta)) - 1) > 1e-12:
+        fails.append("PAC closed form")
+    rho, ks = orc.frequent_plan(1 << 28, k, eps, delta, exact=True)
+    if ks != k or abs(rho * (1 << 28) / (2 / (eps ** 2 * k) * math.log((1 << 28) / delta)) - 1) > 1e-12:
+        fails.append("EC closed form")
+    if orc.frequent_plan(1 << 28, k, eps, delta)[0] != 1.0:
+        fails.append("PAC rho clamp")
+    rho_big_p, ks_big_p = orc.frequent_plan(1 << 40, k, 1e-6, 1e-8, pes=1024, exact=True)
+    if not ks_big_p > k:
+        fails.append("EC k* grows with p")
+    return fails
+
+
 def check_batched_rows(orc, seed=4):
     fails = []
     g = np.random.Generator(np.random.Philox(seed))
@@ -296,4 +440,6 @@ def check_batched_rows(orc, seed=4):
 
 ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_cases,
               check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
-              check_batched_rows, check_delete_min_vs_heap]
+              check_batched_rows, check_delete_min_vs_heap, check_philox_kat,
+              check_pac_worked_example, check_frequent_vs_counter, check_bernoulli_decisions,
+              check_frequent_plan]

@@ -29,6 +29,11 @@ MUTATIONS = {
     "runs_bisection_strict": ("if (run_off[mid] <= g)", "if (run_off[mid] < g)"),
     "delete_ignores_cursor": ("for (i = run_off[r] + cursor[r]; i < run_off[r + 1]; ++i) {",
                               "for (i = run_off[r]; i < run_off[r + 1]; ++i) {"),
+    "freq_tiebreak_reversed": ("return x->obj < y->obj ? -1 : x->obj > y->obj ? 1 : 0;",
+                               "return x->obj < y->obj ? 1 : x->obj > y->obj ? -1 : 0;"),
+    "ec_counts_sample_only": ("            freq[lo].count += 1;", "            freq[lo].count += mask[i];"),
+    "philox_lanes_swapped": ("        c1 = lo1;\n", "        c1 = lo0;\n"),
+    "pac_rate_first_term_only": ("rho_n = 4.0 / (eps * eps) * (a > b ? a : b);", "rho_n = 4.0 / (eps * eps) * a;"),
     "take_k_minus_one": ("for (i = 0; i < k; ++i)             /* ranks 1..k */",
                          "for (i = 1; i < k; ++i)             /* ranks 1..k */"),
 }

@@ -401,6 +401,41 @@ def measure_sorted_runs(tk, wl, torch, ctx):
     return res
 
 
+def measure_frequent(tk, wl, torch, ctx, peak_gbs):
+    """Top-k most frequent objects (Section 7, experiments of Section 10.2):
+    n = 2^28 Zipf objects (s = 1, 2^20 values), k = 32, eps = 3e-4,
+    delta = 1e-4; Algorithm EC at its planned rate, Algorithm PAC at its
+    planned rate (1 on one GPU: every object counted) and at EC's rate."""
+    n = 1 << 28
+    d_obj = wl.device_zipf_objects(n, seed=2024)
+    res = {"workload": "n=2^28 u32 objects, Zipf s=1 over 2^20 values, k=32, eps=3e-4, delta=1e-4"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ec = tk.make_freq_params(32, algorithm=tk.TOPK_FREQ_EC, epsilon=3e-4, delta=1e-4, seed=3)
+    ec_rho, ec_kstar = tk.topk_frequent_plan(n, ec)
+    cases = (("ec", ec, 2),
+             ("pac", tk.make_freq_params(32, algorithm=tk.TOPK_FREQ_PAC, epsilon=3e-4, delta=1e-4, seed=3), 1),
+             ("pac_at_ec_rate", tk.make_freq_params(32, algorithm=tk.TOPK_FREQ_PAC, rho=ec_rho, seed=3), 1))
+    for name, fp, passes in cases:
+        rho, kstar = tk.topk_frequent_plan(n, fp)
+        out = tk.topk_frequent(ctx, d_obj, fp)
+        for _ in range(2):
+            tk.topk_frequent(ctx, d_obj, fp, out=out, check=False)
+        torch.cuda.synchronize()
+        reps = 5
+        e0.record()
+        for _ in range(reps):
+            tk.topk_frequent(ctx, d_obj, fp, out=out, check=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = passes * 4 * n / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "objects_per_s": n / (ms / 1e3), "rho": rho, "kstar": kstar,
+                     "sample_size": int(out[2].view(torch.int64).item()),
+                     "input_passes": passes, "input_gbs": gbs, "frac_of_hbm": gbs / peak_gbs}
+    res["status"] = ctx.sync()
+    return res
+
+
 def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
     uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
@@ -643,6 +678,7 @@ def run_ours(args):
         for key, fn in (("plain", lambda: measure_plain(tk, wl, torch, ctx)),
                         ("batched", lambda: measure_batched(tk, wl, torch, ctx)),
                         ("sorted_runs", lambda: measure_sorted_runs(tk, wl, torch, ctx)),
+                        ("frequent", lambda: measure_frequent(tk, wl, torch, ctx, peak)),
                         ("served", lambda: measure_served(tk, wl, torch))):
             try:
                 line[key] = fn()

@@ -243,6 +243,64 @@ topk_status topk_select_batched(topk_ctx *ctx, const void *d_keys,
                                 void *d_kth_keys, uint32_t *d_kth_idx,
                                 const topk_params *params, void *stream);
 
+/* ---- Top-k most frequent objects (Section 7) ---- */
+
+#define TOPK_FREQ_PAC 0u /* Section 7.1: sample counts of the sampled objects */
+#define TOPK_FREQ_EC 1u  /* Section 7.2: exact counts of the k* candidates */
+
+typedef struct {
+    uint32_t algorithm;    /* TOPK_FREQ_PAC or TOPK_FREQ_EC */
+    uint32_t k;            /* objects returned, >= 1 */
+    double epsilon;        /* accuracy target eps > 0 (error < eps * n) */
+    double delta;          /* failure probability, 0 < delta < 1 */
+    double rho;            /* sampling probability in (0, 1]; 0 = from eps
+                              and delta (PAC: equation sampleSize; EC:
+                              2 ln(n / delta) / (eps^2 k*) objects) */
+    uint32_t kstar;        /* EC: candidates counted exactly, >= k; 0 = from
+                              eps and delta: max(k, sqrt(2 log2(p) / p *
+                              ln(n / delta)) / eps) */
+    uint32_t pes;          /* p of the k* formula; 0 = 1 (one GPU) */
+    uint64_t seed;         /* Philox4x32-10 key of the sample decisions */
+    uint64_t max_distinct; /* most distinct sampled objects the hash table
+                              must hold (it has the next power of two above
+                              twice this many slots, 8 bytes each); 0 = 2^22 */
+} topk_freq_params;
+
+/* Sampling probability rho and k* that topk_frequent would use for n
+ * objects (host only, no device work).  Returns TOPK_EINVAL for a zero k or
+ * n, an unknown algorithm, eps <= 0 or delta outside (0, 1) where they are
+ * needed, rho outside (0, 1], or k* < k. */
+topk_status topk_frequent_plan(uint64_t n, const topk_freq_params *fp, double *rho,
+                               uint32_t *kstar);
+
+/* Top-k most frequent objects of n uint32 objects on one GPU (Section 7):
+ * a Bernoulli sample with probability rho (object i is sampled iff word
+ * i % 4 of Philox4x32-10 at counter (i / 4 low, i / 4 high, 0x53414d50, 0)
+ * and key (seed low, seed high) is below floor(rho * 2^32); every object
+ * when rho = 1) is counted in a hash table (block-local tables in shared
+ * memory flushed into one table in device memory); then
+ *   TOPK_FREQ_PAC (Algorithm PAC): the k most frequently sampled objects,
+ *     d_out_count = their sample counts (the paper's estimate of an
+ *     object's frequency is sample count / rho);
+ *   TOPK_FREQ_EC (Algorithm EC): the k* most frequently sampled objects are
+ *     counted exactly over the whole input, d_out_count = the exact counts
+ *     of the k most frequent of them (k* <= 4096).
+ * "Most frequent" orders by count, larger first, equal counts by the
+ * smaller object, so the result is unique for a given seed.
+ *   d_objects     n uint32 (dtype TOPK_U32), 4-byte aligned, 1 <= n < 2^32 - 1.
+ *   d_out_obj     k uint32, d_out_count k uint64 (caller-owned device
+ *                 memory): the objects and counts, in no particular order.
+ *   d_sample_size NULL or 1 uint64: the number of sampled objects.
+ * The hash table and candidates live in context-owned device memory (grown
+ * on demand).  Returns TOPK_EINVAL for bad arguments (as
+ * topk_frequent_plan, plus k* > 4096 for EC and a NULL pointer).  Reported
+ * by topk_status_sync(): TOPK_EINVAL when fewer than k (PAC) or k* (EC)
+ * distinct objects were sampled, TOPK_ENOMEM when more distinct objects
+ * were sampled than the table holds (raise max_distinct). */
+topk_status topk_frequent(topk_ctx *ctx, const void *d_objects, uint64_t n, topk_dtype dtype,
+                          const topk_freq_params *fp, uint32_t *d_out_obj,
+                          uint64_t *d_out_count, uint64_t *d_sample_size, void *stream);
+
 /* Autotuner of topk_select_batched (no counterpart in the paper): runs the
  * given batch with every candidate block size (256, 512, 1024 threads),
  * sample size (1024, 2048, 4096) and finish threshold (the block's capacity

@@ -43,6 +43,16 @@ class topk_params(ctypes.Structure):
                 ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
 
 
+TOPK_FREQ_PAC = 0
+TOPK_FREQ_EC = 1
+
+
+class topk_freq_params(ctypes.Structure):
+    _fields_ = [("algorithm", ctypes.c_uint32), ("k", ctypes.c_uint32), ("epsilon", ctypes.c_double),
+                ("delta", ctypes.c_double), ("rho", ctypes.c_double), ("kstar", ctypes.c_uint32),
+                ("pes", ctypes.c_uint32), ("seed", ctypes.c_uint64), ("max_distinct", ctypes.c_uint64)]
+
+
 class topk_stats(ctypes.Structure):
     _fields_ = [("levels_grid", ctypes.c_uint32), ("levels_block", ctypes.c_uint32),
                 ("pivot_failures", ctypes.c_uint32), ("overflows", ctypes.c_uint32),
@@ -91,6 +101,12 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_sorted_runs_flexible"):
         lib.topk_select_sorted_runs_flexible.argtypes = [vp, vp, vp, u32, u64, u64, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_sorted_runs_flexible.restype = st
+    if hasattr(lib, "topk_frequent"):
+        lib.topk_frequent_plan.argtypes = [u64, ctypes.POINTER(topk_freq_params), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(u32)]
+        lib.topk_frequent_plan.restype = st
+        lib.topk_frequent.argtypes = [vp, vp, u64, i32, ctypes.POINTER(topk_freq_params), vp, vp, vp, vp]
+        lib.topk_frequent.restype = st
     if hasattr(lib, "topk_runs_delete_min"):
         lib.topk_runs_delete_min.argtypes = [vp, vp, vp, u32, vp, u64, i32, vp, vp, vp, vp, vp]
         lib.topk_runs_delete_min.restype = st
@@ -367,6 +383,44 @@ def topk_runs_delete_min_flexible(ctx: Context, keys, run_off, cursor, kmin: int
     _check(st, "topk_runs_delete_min_flexible")
     if check:
         _check(ctx.sync(stream), "topk_runs_delete_min_flexible (device)")
+    return out
+
+
+def make_freq_params(k: int, algorithm: int = TOPK_FREQ_EC, epsilon: float = 3e-4, delta: float = 1e-4,
+                     rho: float = 0.0, kstar: int = 0, pes: int = 0, seed: int = 0x5EED,
+                     max_distinct: int = 0) -> topk_freq_params:
+    return topk_freq_params(algorithm=algorithm, k=k, epsilon=epsilon, delta=delta, rho=rho, kstar=kstar,
+                            pes=pes, seed=seed, max_distinct=max_distinct)
+
+
+def topk_frequent_plan(n: int, fp: topk_freq_params):
+    """(rho, kstar) that topk_frequent uses for n objects (host only)."""
+    rho = ctypes.c_double()
+    ks = ctypes.c_uint32()
+    _check(load_library().topk_frequent_plan(int(n), ctypes.byref(fp), ctypes.byref(rho), ctypes.byref(ks)),
+           "topk_frequent_plan")
+    return rho.value, ks.value
+
+
+def topk_frequent(ctx: Context, objects, fp: topk_freq_params, stream=None, out=None, check: bool = True):
+    """Top-k most frequent of the uint32 objects (Algorithm PAC or EC,
+    Section 7).  Returns (objects[k] uint32, counts[k] uint64,
+    sample_size[1] uint64); counts are sample counts (PAC) or exact counts
+    (EC); any order."""
+    torch = _torch()
+    if objects.dtype not in (torch.uint32, torch.int32):
+        raise TypeError("objects must be a 32-bit tensor")
+    k = int(fp.k)
+    if out is None:
+        out = (torch.empty(k, dtype=torch.uint32, device=objects.device),
+               torch.empty(k, dtype=torch.uint64, device=objects.device),
+               torch.empty(1, dtype=torch.uint64, device=objects.device))
+    oo, oc, ss = out
+    st = load_library().topk_frequent(ctx.handle, _ptr(objects), objects.numel(), TOPK_U32, ctypes.byref(fp),
+                                      _ptr(oo), _ptr(oc), _ptr(ss), _stream_ptr(stream))
+    _check(st, "topk_frequent")
+    if check:
+        _check(ctx.sync(stream), "topk_frequent (device)")
     return out
 
 

@@ -176,6 +176,7 @@ void topk_ctx_destroy(topk_ctx* ctx) {
         for (int j = 0; j < 2; ++j)
             if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
     if (ctx->scratch.base) cudaFree(ctx->scratch.base);
+    if (ctx->freq.base) cudaFree(ctx->freq.base);
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
 }

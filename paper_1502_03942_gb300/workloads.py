@@ -23,6 +23,12 @@ Recipes (the paper's own experiments use synthetic Zipf data, Section 10.1):
                 run sorted ascending.
   batched     : rows of length floor(2^U(lo, hi)), N(0, 3^2) f32 keys,
                 k uniform on 1..kmax (clamped to the row length).
+  objects     : inputs of the top-k most frequent objects (Section 10.2):
+                Zipf ranks with s = 1 over 2^20 values (the most frequent
+                object j times as frequent as the one of rank j), or the
+                negative binomial distribution with r = 1000, p = 0.05; the
+                object is the value times 0x9E3779B1 mod 2^32 (a bijection,
+                so object order is unrelated to frequency).
 """
 from __future__ import annotations
 
@@ -119,7 +125,36 @@ def batched_rows(rows: int, lo: float, hi: float, kmax: int, seed: int,
     return keys, off, ks
 
 
+OBJECT_SCRAMBLE = 0x9E3779B1
+
+
+def zipf_objects(n: int, seed: int, s: float = 1.0, support: int = 1 << 20) -> np.ndarray:
+    r = zipf_ranks(n, seed, s, support).astype(np.uint64)
+    return ((r * OBJECT_SCRAMBLE) & 0xFFFFFFFF).astype(np.uint32)
+
+
+def negbin_objects(n: int, seed: int, r: int = 1000, p: float = 0.05) -> np.ndarray:
+    v = rng(seed).negative_binomial(r, p, size=n).astype(np.uint64)
+    return ((v * OBJECT_SCRAMBLE) & 0xFFFFFFFF).astype(np.uint32)
+
+
 # ---------------------------------------------------------------- device side
+
+def device_zipf_objects(n: int, seed: int, s: float = 1.0, support: int = 1 << 20, device="cuda"):
+    """zipf_objects drawn on the device with torch (benchmark inputs)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    cdf = torch.from_numpy(zipf_cdf(s, support)).to(device)
+    out = torch.empty(n, dtype=torch.int32, device=device)
+    step = 1 << 26
+    for a in range(0, n, step):
+        m = min(step, n - a)
+        u = torch.rand(m, generator=g, device=device, dtype=torch.float64)
+        r = torch.clamp(torch.searchsorted(cdf, u, right=True) + 1, max=support).to(torch.int64)
+        o = (r * OBJECT_SCRAMBLE) & 0xFFFFFFFF
+        out[a:a + m] = torch.where(o >= (1 << 31), o - (1 << 32), o).to(torch.int32)
+    return out.view(torch.uint32)
 
 def device_f32_dataset(name: str, n: int, seed: int, device="cuda"):
     """Same recipes drawn on the device with torch (benchmark inputs)."""

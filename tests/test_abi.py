@@ -74,6 +74,8 @@ def test_struct_layouts_match_binding(tmp_path):
                    '  printf("%zu %zu\\n", sizeof(topk_stats), offsetof(topk_stats, sample_kept));\n'
                    '  printf("%zu %zu\\n", sizeof(topk_request), offsetof(topk_request, arrival_ns));\n'
                    '  printf("%zu %zu\\n", sizeof(topk_serve_report), offsetof(topk_serve_report, elapsed_s));\n'
+                   '  printf("%zu %zu %zu\\n", sizeof(topk_freq_params), offsetof(topk_freq_params, seed),'
+                   " offsetof(topk_freq_params, max_distinct));\n"
                    "  return 0;\n}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -83,6 +85,8 @@ def test_struct_layouts_match_binding(tmp_path):
     assert got[1] == [ctypes.sizeof(tk.topk_stats), tk.topk_stats.sample_kept.offset]
     assert got[2] == [ctypes.sizeof(tk.topk_request), tk.topk_request.arrival_ns.offset]
     assert got[3] == [ctypes.sizeof(tk.topk_serve_report), tk.topk_serve_report.elapsed_s.offset]
+    assert got[4] == [ctypes.sizeof(tk.topk_freq_params), tk.topk_freq_params.seed.offset,
+                      tk.topk_freq_params.max_distinct.offset]
 
 
 def test_tuning_calls_reject_bad_arguments(lib):

@@ -24,9 +24,9 @@ constexpr u64 FQ_EMPTY = ~0ull;
 constexpr u32 FQ_STREAM = 0x53414d50u; // counter word 2 of the sampling stream
 constexpr int FQ_NT = 512;              // threads of the counting kernels
 constexpr int FQ_QUADS = 4;             // 4-object groups per thread per tile
-constexpr int FQ_LOCAL_LOG = 12;        // block-local table: 4096 slots
+constexpr int FQ_LOCAL_LOG = 12;        // block-local table: 4096 slots (32 KB)
 constexpr int FQ_LOCAL = 1 << FQ_LOCAL_LOG;
-constexpr int FQ_LOCAL_PROBES = 16;
+constexpr int FQ_LOCAL_PROBES = 4;
 constexpr u32 FQ_EXACT_MAX = 4096;      // largest k* of the exact recount
 constexpr u64 FQ_DEFAULT_DISTINCT = 1ull << 22;
 
@@ -64,16 +64,24 @@ __device__ bool fq_table_add(u64* table, u32 mask, u32 obj, u32 c) {
     return false;
 }
 
+// Block-local table and per-warp queues of the counting kernel.  Objects
+// claim slots of the local table until it is full and keep them (no flush
+// before the end): the frequent objects, which appear early and often, are
+// then counted in shared memory, and an object that finds neither itself
+// nor a free slot within FQ_LOCAL_PROBES goes straight to the HBM table.
+// The queue packs a warp's sampled objects so that every lane inserts one
+// (at a sampling rate well below 1 most lanes of a quad sample nothing).
+constexpr int FQ_QCAP = FQ_QUADS * 4 * 32;
+
 struct FqLocal {
     u64 slot[FQ_LOCAL];
-    u32 fill;      // slots claimed since the last flush
-    u32 flush;     // flush decision of this tile
+    u32 queue[FQ_NT / 32][FQ_QCAP];
     u32 warp_sum[FQ_NT / 32];
 };
 
 // One occurrence into the block-local table (probing from the hash's high
-// bits, independent of the HBM table's position); false after
-// FQ_LOCAL_PROBES occupied slots.
+// bits, independent of the HBM table's position); false when neither the
+// object nor a free slot is found within FQ_LOCAL_PROBES slots.
 __device__ __forceinline__ bool fq_local_add(FqLocal& L, u32 obj) {
     u32 h = fq_mix(obj) >> (32 - FQ_LOCAL_LOG);
 #pragma unroll 1
@@ -82,10 +90,7 @@ __device__ __forceinline__ bool fq_local_add(FqLocal& L, u32 obj) {
         if (w == FQ_EMPTY) {
             const u64 prev =
                 atomicCAS(reinterpret_cast<unsigned long long*>(&L.slot[h]), FQ_EMPTY, fq_word(obj, 1));
-            if (prev == FQ_EMPTY) {
-                atomicAdd(&L.fill, 1u);
-                return true;
-            }
+            if (prev == FQ_EMPTY) return true;
             w = prev;
         }
         if ((u32)w == obj) {
@@ -100,98 +105,171 @@ __device__ __forceinline__ bool fq_local_add(FqLocal& L, u32 obj) {
 struct FreqArgs {
     const u32* obj;
     u64 n;
-    u64 thr;       // sampled iff Philox word < thr (2^32: every object)
+    u32 thr;              // sampled iff Philox word < thr (unused when every object is)
     u32 seed_lo, seed_hi;
     u64* table;
-    u32 mask;      // table slots - 1
-    u64* sample_size;
+    u32 mask;             // table slots - 1
+    u64* sampled;         // sample size (zeroed before)
     u32* err;
 };
 
+// Moves every entry of the block-local table into the HBM table.  Each
+// thread takes FQ_LOCAL / FQ_NT slots, four at a time, and reads their home
+// positions in the HBM table at once; an object found at its home position
+// costs one atomic add, the rest probe.
 __device__ __forceinline__ void fq_flush(FqLocal& L, const FreqArgs& a) {
-    for (u32 s = threadIdx.x; s < FQ_LOCAL; s += FQ_NT) {
-        const u64 w = L.slot[s];
-        if (w != FQ_EMPTY) {
-            if (!fq_table_add(a.table, a.mask, (u32)w, 0xFFFFFFFFu - (u32)(w >> 32)))
+    constexpr int G = 4;
+#pragma unroll 1
+    for (u32 base = threadIdx.x; base < FQ_LOCAL; base += G * FQ_NT) {
+        u64 mine[G], seen[G];
+        u32 pos[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            mine[j] = L.slot[base + j * FQ_NT];
+            pos[j] = fq_mix((u32)mine[j]) & a.mask;
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) seen[j] = mine[j] != FQ_EMPTY ? __ldcg(a.table + pos[j]) : FQ_EMPTY;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (mine[j] == FQ_EMPTY) continue;
+            const u32 obj = (u32)mine[j], c = 0xFFFFFFFFu - (u32)(mine[j] >> 32);
+            if (seen[j] != FQ_EMPTY && (u32)seen[j] == obj) {
+                atomicAdd(reinterpret_cast<unsigned long long*>(a.table + pos[j]),
+                          (unsigned long long)(0ull - ((u64)c << 32)));
+            } else if (!fq_table_add(a.table, a.mask, obj, c)) {
                 atomicCAS(a.err, 0u, (u32)TOPK_ENOMEM);
-            L.slot[s] = FQ_EMPTY;
+            }
         }
     }
 }
 
-// Sampling and counting (Section 7.1): every block walks tiles of
-// FQ_NT * FQ_QUADS * 4 objects; object i is sampled iff word i % 4 of
-// Philox4x32-10 at counter (i / 4, FQ_STREAM) is below the threshold.
-// Sampled objects go to the block-local table, which is flushed into the
-// HBM table whenever it is more than half full, and at the end.
+__device__ __forceinline__ void fq_insert(FqLocal& L, const FreqArgs& a, u32 obj) {
+    if (!fq_local_add(L, obj) && !fq_table_add(a.table, a.mask, obj, 1)) atomicCAS(a.err, 0u, (u32)TOPK_ENOMEM);
+}
+
+// Loads the FQ_QUADS quads of one tile (all loads in flight at once);
+// FULL: the tile lies inside the objects and they are 16-byte aligned.
+template <bool FULL, bool VEC>
+__device__ __forceinline__ void fq_load_tile(const u32* obj, u64 n, u64 q0, uint4 (&x)[FQ_QUADS]) {
+#pragma unroll
+    for (int j = 0; j < FQ_QUADS; ++j) {
+        const u64 q = q0 + (u64)j * FQ_NT;
+        const u64 i0 = q * 4;
+        if (FULL || (VEC && i0 + 4 <= n)) {
+            x[j] = ld_stream(reinterpret_cast<const uint4*>(obj) + q);
+        } else {
+            x[j].x = i0 + 0 < n ? __ldcs(obj + i0 + 0) : 0u;
+            x[j].y = i0 + 1 < n ? __ldcs(obj + i0 + 1) : 0u;
+            x[j].z = i0 + 2 < n ? __ldcs(obj + i0 + 2) : 0u;
+            x[j].w = i0 + 3 < n ? __ldcs(obj + i0 + 3) : 0u;
+        }
+    }
+}
+
+__device__ __forceinline__ u32 u4at(const uint4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+
+// One tile: sample decisions for the thread's FQ_QUADS * 4 objects (bit
+// 4j + e = object e of quad j); every sampled object is inserted, through
+// the warp's queue unless every object is sampled.  Returns the number of
+// objects this thread sampled.
+template <bool ALL, bool FULL, bool VEC>
+__device__ __forceinline__ u32 fq_tile(FqLocal& L, const FreqArgs& a, u64 q0, u32* queue, u32 lane) {
+    uint4 x[FQ_QUADS];
+    fq_load_tile<FULL, VEC>(a.obj, a.n, q0, x);
+    u32 take = 0;
+#pragma unroll
+    for (int j = 0; j < FQ_QUADS; ++j) {
+        const u64 q = q0 + (u64)j * FQ_NT;
+        u32 t4 = 0xF;
+        if (!ALL) {
+            const Philox4 r = philox4x32_10((u32)q, (u32)(q >> 32), FQ_STREAM, 0u, a.seed_lo, a.seed_hi);
+            t4 = (r.v[0] < a.thr ? 1u : 0u) | (r.v[1] < a.thr ? 2u : 0u) | (r.v[2] < a.thr ? 4u : 0u) |
+                 (r.v[3] < a.thr ? 8u : 0u);
+        }
+        if (!FULL) {
+            const u64 i0 = q * 4;
+            t4 = i0 >= a.n ? 0u : i0 + 4 > a.n ? t4 & ((1u << (u32)(a.n - i0)) - 1u) : t4;
+        }
+        take |= t4 << (4 * j);
+    }
+    const u32 c = __popc(take);
+    if (ALL) {
+#pragma unroll
+        for (int j = 0; j < FQ_QUADS; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (FULL || ((take >> (4 * j + e)) & 1u)) fq_insert(L, a, u4at(x[j], e));
+        return c;
+    }
+    u32 incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (u32)o) incl += y;
+    }
+    const u32 total = __shfl_sync(0xffffffffu, incl, 31);
+    u32 at = incl - c;
+#pragma unroll
+    for (int j = 0; j < FQ_QUADS; ++j)
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if ((take >> (4 * j + e)) & 1u) queue[at++] = u4at(x[j], e);
+    __syncwarp();
+    for (u32 i = lane; i < total; i += 32) fq_insert(L, a, queue[i]);
+    __syncwarp();
+    return c;
+}
+
+// Sampling and counting (Section 7.1) in one pass: every block walks tiles
+// of FQ_NT * FQ_QUADS * 4 objects; object i is sampled iff word i % 4 of
+// Philox4x32-10 at counter (i / 4, FQ_STREAM) and the seed's key is below
+// the threshold.  No block barrier until the final flush of the local
+// table into the HBM table.
 template <bool ALL, bool VEC>
-__global__ void __launch_bounds__(FQ_NT) k_freq_count(FreqArgs a) {
-    __shared__ FqLocal L;
+__global__ void __launch_bounds__(FQ_NT, 3) k_freq_count(FreqArgs a) {
+    extern __shared__ __align__(16) unsigned char fq_dyn[];
+    FqLocal& L = *reinterpret_cast<FqLocal*>(fq_dyn);
     for (u32 s = threadIdx.x; s < FQ_LOCAL; s += FQ_NT) L.slot[s] = FQ_EMPTY;
-    if (threadIdx.x == 0) L.fill = 0;
     grid_dep_wait(); // the table was cleared by the previous operation
     __syncthreads();
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u32* queue = L.queue[warp];
     const u64 quads = (a.n + 3) / 4;
     const u64 tile_quads = (u64)FQ_NT * FQ_QUADS;
     const u64 tiles = (quads + tile_quads - 1) / tile_quads;
-    u64 sampled = 0;
+    const u64 full_tiles = VEC ? (a.n / 4) / tile_quads : 0;
+    u32 sampled = 0;
     for (u64 t = blockIdx.x; t < tiles; t += gridDim.x) {
-#pragma unroll
-        for (int j = 0; j < FQ_QUADS; ++j) {
-            const u64 q = t * tile_quads + (u64)j * FQ_NT + threadIdx.x;
-            if (q >= quads) break;
-            const u64 i0 = q * 4;
-            u32 v[4];
-            if (VEC && i0 + 4 <= a.n) {
-                const uint4 x = ld_stream(reinterpret_cast<const uint4*>(a.obj) + q);
-                v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
-            } else {
-#pragma unroll
-                for (int e = 0; e < 4; ++e) v[e] = i0 + e < a.n ? __ldcs(a.obj + i0 + e) : 0u;
-            }
-            u32 take = 0;
-            if (ALL) {
-                take = 0xF;
-            } else {
-                const Philox4 r = philox4x32_10((u32)q, (u32)(q >> 32), FQ_STREAM, 0u, a.seed_lo, a.seed_hi);
-#pragma unroll
-                for (int e = 0; e < 4; ++e) take |= ((u64)r.v[e] < a.thr ? 1u : 0u) << e;
-            }
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (!((take >> e) & 1u) || i0 + e >= a.n) continue;
-                ++sampled;
-                if (!fq_local_add(L, v[e]) && !fq_table_add(a.table, a.mask, v[e], 1))
-                    atomicCAS(a.err, 0u, (u32)TOPK_ENOMEM);
-            }
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) L.flush = L.fill > FQ_LOCAL / 2 ? 1u : 0u;
-        __syncthreads();
-        if (L.flush) {
-            fq_flush(L, a);
-            if (threadIdx.x == 0) L.fill = 0;
-            __syncthreads();
-        }
+        const u64 q0 = t * tile_quads + threadIdx.x;
+        if (t < full_tiles) sampled += fq_tile<ALL, true, VEC>(L, a, q0, queue, lane);
+        else sampled += fq_tile<ALL, false, VEC>(L, a, q0, queue, lane);
     }
+    __syncthreads();
     fq_flush(L, a);
     // sample size: warp sums, then one atomic per block
-    u64 w = sampled;
+    u32 w = sampled;
     for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) L.warp_sum[threadIdx.x >> 5] = (u32)w;
+    if (lane == 0) L.warp_sum[warp] = w;
     __syncthreads();
     if (threadIdx.x == 0) {
         u64 s = 0;
         for (int i = 0; i < FQ_NT / 32; ++i) s += L.warp_sum[i];
-        if (a.sample_size) atomicAdd(reinterpret_cast<unsigned long long*>(a.sample_size), (unsigned long long)s);
+        atomicAdd(reinterpret_cast<unsigned long long*>(a.sampled), (unsigned long long)s);
     }
 }
 
 // Exact recount of the k* candidates (Section 7.2) over the whole input:
-// the candidates sit in a shared-memory hash table (object, candidate
-// number); every block counts its tiles in shared memory and adds its
-// counts to exact[] at the end.
+// the candidates sit in a shared-memory hash table of words
+// (candidate number << 32 | object); every block counts its part and adds its counts to exact[] at
+// the end.  The candidates are the most frequent objects, so many threads
+// hit the same few counters: MODE 0 (k* <= FQ_PT_MAX) gives every thread
+// its own counters (plain increments), MODE 1 (k* <= FQ_PW_MAX) every warp
+// (shared-memory atomics within the warp only), MODE 2 one set per block.
+constexpr u32 FQ_PT_MAX = 32;
+constexpr int FQ_XQUADS = 4; // 4-object groups per thread per iteration (loads in flight)
+constexpr u32 FQ_PW_MAX = 1024;
+
 struct ExactArgs {
     const u32* obj;
     u64 n;
@@ -201,47 +279,96 @@ struct ExactArgs {
     u32* exact;      // kstar counts (zeroed before)
 };
 
-template <bool VEC>
-__global__ void __launch_bounds__(FQ_NT) k_freq_exact(ExactArgs a) {
+__host__ __device__ inline size_t fq_exact_counters(int mode, u32 kstar) {
+    return mode == 0 ? (size_t)kstar * FQ_NT : mode == 1 ? (size_t)kstar * (FQ_NT / 32) : (size_t)kstar;
+}
+
+// Position of an object in the recount's candidate table: one
+// multiplication (the table holds at most a few thousand candidates and is
+// at least four times larger, so a cheap hash keeps probes short).
+__device__ __forceinline__ u32 fq_cand_pos(u32 v, u32 log_slots) { return (v * 0x2545F491u) >> (32 - log_slots); }
+
+// Counts one object: a table word is (candidate number << 32) | object, an
+// empty slot has a negative candidate number.
+template <int MODE>
+__device__ __forceinline__ void fq_recount_one(const u64* slot, u32 log_slots, u32* my, u32 v) {
+    const u32 mask = (1u << log_slots) - 1;
+    u32 h = fq_cand_pos(v, log_slots);
+    u64 w = slot[h];
+    int c = (int)(w >> 32);
+    if (c >= 0 && (u32)w != v) {
+        do {
+            h = (h + 1) & mask;
+            w = slot[h];
+            c = (int)(w >> 32);
+        } while (c >= 0 && (u32)w != v);
+    }
+    if (c >= 0) {
+        if (MODE == 0) my[(u32)c * FQ_NT] += 1;
+        else atomicAdd(&my[c], 1u);
+    }
+}
+
+template <int MODE, bool VEC>
+__global__ void __launch_bounds__(FQ_NT, 3) k_freq_exact(ExactArgs a) {
     extern __shared__ __align__(16) unsigned char fq_smem[];
     const u32 slots = 1u << a.log_slots;
-    u32* key = reinterpret_cast<u32*>(fq_smem);
-    int* id = reinterpret_cast<int*>(key + slots);
-    u32* cnt = reinterpret_cast<u32*>(id + slots);
-    for (u32 s = threadIdx.x; s < slots; s += FQ_NT) id[s] = -1;
-    for (u32 c = threadIdx.x; c < a.kstar; c += FQ_NT) cnt[c] = 0;
+    u64* slot = reinterpret_cast<u64*>(fq_smem);
+    u32* cnt = reinterpret_cast<u32*>(slot + slots);
+    const u32 ncnt = (u32)fq_exact_counters(MODE, a.kstar);
+    for (u32 s = threadIdx.x; s < slots; s += FQ_NT) slot[s] = ~0ull;
+    for (u32 c = threadIdx.x; c < ncnt; c += FQ_NT) cnt[c] = 0;
     grid_dep_wait(); // the candidates come from the previous selection
     __syncthreads();
     for (u32 c = threadIdx.x; c < a.kstar; c += FQ_NT) {
         const u32 o = (u32)a.cand[c];
-        u32 h = fq_mix(o) >> (32 - a.log_slots);
-        while (atomicCAS(&id[h], -1, (int)c) != -1) h = (h + 1) & (slots - 1);
-        key[h] = o;
+        const u64 word = ((u64)c << 32) | o;
+        u32 h = fq_cand_pos(o, a.log_slots);
+        while (atomicCAS(reinterpret_cast<unsigned long long*>(&slot[h]), ~0ull, word) != ~0ull)
+            h = (h + 1) & (slots - 1);
     }
     __syncthreads();
+    // this thread's (MODE 0) or warp's (MODE 1) counters
+    u32* my = MODE == 0 ? cnt + threadIdx.x : MODE == 1 ? cnt + (threadIdx.x >> 5) * a.kstar : cnt;
     const u64 quads = (a.n + 3) / 4;
-    for (u64 q = (u64)blockIdx.x * FQ_NT + threadIdx.x; q < quads; q += (u64)gridDim.x * FQ_NT) {
-        const u64 i0 = q * 4;
-        u32 v[4];
-        if (VEC && i0 + 4 <= a.n) {
-            const uint4 x = ld_stream(reinterpret_cast<const uint4*>(a.obj) + q);
-            v[0] = x.x, v[1] = x.y, v[2] = x.z, v[3] = x.w;
+    const u64 tile_quads = (u64)FQ_NT * FQ_XQUADS;
+    const u64 full_tiles = VEC ? (a.n / 4) / tile_quads : 0;
+    for (u64 t = blockIdx.x; t * tile_quads < quads; t += gridDim.x) {
+        const u64 q0 = t * tile_quads + threadIdx.x;
+        uint4 x[FQ_XQUADS];
+        if (t < full_tiles) {
+#pragma unroll
+            for (int j = 0; j < FQ_XQUADS; ++j) x[j] = ld_stream(reinterpret_cast<const uint4*>(a.obj) + q0 + j * FQ_NT);
+#pragma unroll
+            for (int j = 0; j < FQ_XQUADS; ++j) {
+                fq_recount_one<MODE>(slot, a.log_slots, my, x[j].x);
+                fq_recount_one<MODE>(slot, a.log_slots, my, x[j].y);
+                fq_recount_one<MODE>(slot, a.log_slots, my, x[j].z);
+                fq_recount_one<MODE>(slot, a.log_slots, my, x[j].w);
+            }
         } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) v[e] = i0 + e < a.n ? __ldcs(a.obj + i0 + e) : 0u;
-        }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            if (i0 + e >= a.n) break;
-            u32 h = fq_mix(v[e]) >> (32 - a.log_slots);
-            int c;
-            while ((c = id[h]) >= 0 && key[h] != v[e]) h = (h + 1) & (slots - 1);
-            if (c >= 0) atomicAdd(&cnt[c], 1u);
+            for (int j = 0; j < FQ_XQUADS; ++j) {
+                const u64 i0 = (q0 + (u64)j * FQ_NT) * 4;
+                for (int e = 0; e < 4; ++e)
+                    if (i0 + e < a.n) fq_recount_one<MODE>(slot, a.log_slots, my, __ldcs(a.obj + i0 + e));
+            }
         }
     }
     __syncthreads();
-    for (u32 c = threadIdx.x; c < a.kstar; c += FQ_NT)
-        if (cnt[c]) atomicAdd(&a.exact[c], cnt[c]);
+    if (MODE == 2) {
+        for (u32 c = threadIdx.x; c < a.kstar; c += FQ_NT)
+            if (cnt[c]) atomicAdd(&a.exact[c], cnt[c]);
+        return;
+    }
+    // sum the private counters of each candidate: one warp per candidate
+    const u32 lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const u32 copies = MODE == 0 ? FQ_NT : FQ_NT / 32;
+    for (u32 c = warp; c < a.kstar; c += FQ_NT / 32) {
+        u32 sum = 0;
+        for (u32 t = lane; t < copies; t += 32) sum += MODE == 0 ? cnt[c * FQ_NT + t] : cnt[t * a.kstar + c];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0 && sum) atomicAdd(&a.exact[c], sum);
+    }
 }
 
 // Table words of the candidates with their exact counts.
@@ -253,10 +380,14 @@ __global__ void k_freq_compose(const u64* cand, const u32* exact, u32 kstar, u64
 
 // Selected table words -> objects and counts; a selected empty slot means
 // fewer than `need` distinct objects were sampled.
-__global__ void k_freq_decode(const u64* sel, const u64* kth, u32 k, u32* out_obj, u64* out_cnt, u32* err) {
+// Also writes the sample size: the sampler's cursor, or n when every
+// object was taken.
+__global__ void k_freq_decode(const u64* sel, const u64* kth, u32 k, u32* out_obj, u64* out_cnt, u32* err,
+                              const u64* cursor, u64 all_n, u64* sample_size) {
     grid_dep_wait();
     const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0 && *kth == FQ_EMPTY) atomicCAS(err, 0u, (u32)TOPK_EINVAL);
+    if (i == 0 && sample_size) *sample_size = cursor ? *cursor : all_n;
     if (i < k && out_obj) {
         const u64 w = sel[i];
         out_obj[i] = (u32)w;
@@ -315,6 +446,11 @@ static u32 ceil_log2(u64 x) {
     return l;
 }
 
+// Candidate table of the recount: at most one slot in eight used up to
+// 2048 candidates (short probes for the many objects that are not
+// candidates), 16384 slots above.
+static u32 fq_exact_log_slots(u32 kstar) { return std::min<u32>(14, std::max<u32>(8, ceil_log2(8ull * kstar))); }
+
 static topk_status ensure_freq(topk_ctx* ctx, size_t bytes) {
     Scratch& s = ctx->freq;
     if (s.bytes >= bytes) return TOPK_OK;
@@ -364,11 +500,15 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
 
+    const u64 thr = rho >= 1.0 ? (1ull << 32) : (u64)std::floor(std::ldexp(rho, 32));
+    const bool all = thr >= (1ull << 32);
+
     Carve cv;
     const size_t o_table = cv.take(8 * cap);
     const size_t o_sel = cv.take(8ull * need), o_idx = cv.take(4ull * need), o_kth = cv.take(16);
     const size_t o_exact = cv.take(4ull * kstar), o_comp = cv.take(8ull * kstar);
     const size_t o_sel2 = cv.take(8ull * fp->k), o_idx2 = cv.take(4ull * fp->k), o_kth2 = cv.take(16);
+    const size_t o_cursor = cv.take(8);
     rs = ensure_freq(ctx, cv.off);
     if (rs != TOPK_OK) return rs;
     char* base = static_cast<char*>(ctx->freq.base);
@@ -377,70 +517,89 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
     u32* sel_idx = reinterpret_cast<u32*>(base + o_idx);
     u64* kth = reinterpret_cast<u64*>(base + o_kth);
     u32* kth_idx = reinterpret_cast<u32*>(base + o_kth + 8);
+    u64* cursor = reinterpret_cast<u64*>(base + o_cursor); // sample size
 
-    // 1. sample and count (Section 7.1)
+    static std::atomic<uint64_t> count_attr{0};
+    const uint64_t dbit = 1ull << (ctx->device & 63);
+    if (!(count_attr.load() & dbit)) {
+        for (auto kf : {k_freq_count<true, true>, k_freq_count<true, false>, k_freq_count<false, true>,
+                        k_freq_count<false, false>})
+            if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(FqLocal)) !=
+                cudaSuccess)
+                return TOPK_ECUDA;
+        count_attr.fetch_or(dbit);
+    }
+
+    // 1.-2. sample and count (Section 7.1)
     cudaError_t e = cudaMemsetAsync(table, 0xFF, 8 * cap, st);
-    if (e == cudaSuccess && d_sample_size) e = cudaMemsetAsync(d_sample_size, 0, 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, 8, st);
     if (e != cudaSuccess) return cuda_status(e);
+    const bool vec = reinterpret_cast<uintptr_t>(d_objects) % 16 == 0;
     FreqArgs a{};
     a.obj = static_cast<const u32*>(d_objects);
     a.n = n;
-    a.thr = rho >= 1.0 ? (1ull << 32) : (u64)std::floor(std::ldexp(rho, 32));
+    a.thr = all ? 0u : (u32)thr;
     a.seed_lo = (u32)fp->seed;
     a.seed_hi = (u32)(fp->seed >> 32);
     a.table = table;
     a.mask = (u32)(cap - 1);
-    a.sample_size = d_sample_size;
+    a.sampled = cursor;
     a.err = ctx->d_err;
-    const bool all = a.thr >= (1ull << 32);
-    const bool vec = reinterpret_cast<uintptr_t>(d_objects) % 16 == 0;
     auto kern = all ? (vec ? k_freq_count<true, true> : k_freq_count<true, false>)
                     : (vec ? k_freq_count<false, true> : k_freq_count<false, false>);
     int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FQ_NT, 0);
-    const u64 tiles = ((n + 3) / 4 + (u64)FQ_NT * FQ_QUADS - 1) / ((u64)FQ_NT * FQ_QUADS);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FQ_NT, sizeof(FqLocal));
+    const u64 tile_objs = (u64)FQ_NT * FQ_QUADS * 4;
+    const u64 tiles = (n + tile_objs - 1) / tile_objs;
     const int grid = (int)std::max<u64>(1, std::min<u64>(tiles, (u64)ctx->sms * std::max(per_sm, 1)));
-    e = launch_dep(kern, grid, FQ_NT, 0, st, a);
+    e = launch_dep(kern, grid, FQ_NT, sizeof(FqLocal), st, a);
     if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx);
 
-    // 2. the `need` most frequently sampled objects: the smallest table words
+    // 3. the `need` most frequently sampled objects: the smallest table words
     rs = topk_select(ctx, table, cap, need, TOPK_U64, sel, sel_idx, kth, kth_idx, nullptr, stream);
     if (rs != TOPK_OK) return rs;
     if (!ec) {
         e = launch_dep(k_freq_decode, (int)((fp->k + 255) / 256), 256, 0, st, (const u64*)sel, (const u64*)kth,
-                       fp->k, d_out_obj, d_out_count, ctx->d_err);
+                       fp->k, d_out_obj, d_out_count, ctx->d_err, (const u64*)cursor,
+                       (u64)n, d_sample_size);
         count_launch(ctx);
         return cuda_status(e);
     }
-    // 3. EC: exact recount of the k* candidates (Section 7.2)
+    // 4. EC: exact recount of the k* candidates (Section 7.2)
     e = launch_dep(k_freq_check, 1, 32, 0, st, (const u64*)kth, ctx->d_err);
     u32* exact = reinterpret_cast<u32*>(base + o_exact);
     if (e == cudaSuccess) e = cudaMemsetAsync(exact, 0, 4ull * kstar, st);
     if (e != cudaSuccess) return cuda_status(e);
     ExactArgs x{};
-    x.obj = a.obj;
+    x.obj = static_cast<const u32*>(d_objects);
     x.n = n;
     x.cand = sel;
     x.kstar = kstar;
-    x.log_slots = std::max<u32>(6, ceil_log2(2ull * kstar));
+    x.log_slots = fq_exact_log_slots(kstar);
     x.exact = exact;
-    const size_t smem = (size_t)(1u << x.log_slots) * 8 + 4ull * kstar;
-    auto ek = vec ? k_freq_exact<true> : k_freq_exact<false>;
+    const int mode = kstar <= FQ_PT_MAX ? 0 : kstar <= FQ_PW_MAX ? 1 : 2;
+    const size_t smem = (size_t)(1u << x.log_slots) * 8 + 4 * fq_exact_counters(mode, kstar);
+    void (*exact_kernels[3][2])(ExactArgs) = {{k_freq_exact<0, false>, k_freq_exact<0, true>},
+                                              {k_freq_exact<1, false>, k_freq_exact<1, true>},
+                                              {k_freq_exact<2, false>, k_freq_exact<2, true>}};
+    auto ek = exact_kernels[mode][vec ? 1 : 0];
     static std::atomic<uint64_t> attr_mask{0};
     const uint64_t bit = 1ull << (ctx->device & 63);
     if (!(attr_mask.load() & bit)) {
-        const int max_smem = (int)((1u << ceil_log2(2ull * FQ_EXACT_MAX)) * 8 + 4ull * FQ_EXACT_MAX);
-        if (cudaFuncSetAttribute(k_freq_exact<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_freq_exact<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
-                cudaSuccess)
-            return TOPK_ECUDA;
+        for (int m = 0; m < 3; ++m) {
+            const u32 kmax = m == 0 ? FQ_PT_MAX : m == 1 ? FQ_PW_MAX : FQ_EXACT_MAX;
+            const int max_smem = (int)((1u << fq_exact_log_slots(kmax)) * 8 + 4 * fq_exact_counters(m, kmax));
+            for (int v = 0; v < 2; ++v)
+                if (cudaFuncSetAttribute(exact_kernels[m][v], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem) != cudaSuccess)
+                    return TOPK_ECUDA;
+        }
         attr_mask.fetch_or(bit);
     }
     int per_sm_x = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_x, ek, FQ_NT, smem);
-    const u64 quad_blocks = ((n + 3) / 4 + FQ_NT - 1) / FQ_NT;
+    const u64 quad_blocks = ((n + 3) / 4 + (u64)FQ_NT * FQ_XQUADS - 1) / ((u64)FQ_NT * FQ_XQUADS);
     const int grid_x = (int)std::max<u64>(1, std::min<u64>(quad_blocks, (u64)ctx->sms * std::max(per_sm_x, 1)));
     e = launch_dep(ek, grid_x, FQ_NT, smem, st, x);
     u64* comp = reinterpret_cast<u64*>(base + o_comp);
@@ -449,7 +608,7 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
                        kstar, comp);
     if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx, 3);
-    // 4. the k most frequent candidates by exact count
+    // 5. the k most frequent candidates by exact count
     u64* sel2 = reinterpret_cast<u64*>(base + o_sel2);
     u32* idx2 = reinterpret_cast<u32*>(base + o_idx2);
     u64* kth2 = reinterpret_cast<u64*>(base + o_kth2);
@@ -457,7 +616,8 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
     rs = topk_select(ctx, comp, kstar, fp->k, TOPK_U64, sel2, idx2, kth2, kth2_idx, nullptr, stream);
     if (rs != TOPK_OK) return rs;
     e = launch_dep(k_freq_decode, (int)((fp->k + 255) / 256), 256, 0, st, (const u64*)sel2, (const u64*)kth2, fp->k,
-                   d_out_obj, d_out_count, ctx->d_err);
+                   d_out_obj, d_out_count, ctx->d_err, (const u64*)cursor, (u64)n,
+                   d_sample_size);
     count_launch(ctx);
     return cuda_status(e);
 }

@@ -55,6 +55,8 @@ class Oracle:
         lib.oracle_sort_order.restype = i32
         lib.oracle_select.argtypes = [vp, u64, i32, u64, vp, vp]
         lib.oracle_select.restype = i32
+        lib.oracle_select_largest.argtypes = [vp, u64, i32, u64, vp, vp]
+        lib.oracle_select_largest.restype = i32
         lib.oracle_select_runs.argtypes = [vp, vp, u32, u64, vp, vp, vp]
         lib.oracle_select_runs.restype = i32
         lib.oracle_runs_delete_min.argtypes = [vp, vp, u32, vp, u64, vp, vp]
@@ -94,6 +96,17 @@ class Oracle:
         if self.lib.oracle_select(_ptr(a), a.size, DTYPE_CODES[dtype], int(k),
                                   _ptr(sel), _ptr(kth)) != 0:
             raise ValueError("oracle_select rejected its arguments")
+        return sel[: int(k)], int(kth[0])
+
+    def select_largest(self, keys: np.ndarray, dtype: str, k: int):
+        """(sel_idx in descending value order, kth_idx) of the k largest;
+        equal values by ascending position."""
+        a = _bits(keys, dtype)
+        sel = np.empty(max(int(k), 1), np.uint32)
+        kth = np.zeros(1, np.uint32)
+        if self.lib.oracle_select_largest(_ptr(a), a.size, DTYPE_CODES[dtype], int(k), _ptr(sel),
+                                          _ptr(kth)) != 0:
+            raise ValueError("oracle_select_largest rejected its arguments")
         return sel[: int(k)], int(kth[0])
 
     def select_runs(self, keys: np.ndarray, run_off: np.ndarray, k: int):
@@ -205,6 +218,10 @@ def sort_order(keys, dtype):
 
 def select(keys, dtype, k):
     return default().select(keys, dtype, k)
+
+
+def select_largest(keys, dtype, k):
+    return default().select_largest(keys, dtype, k)
 
 
 def select_runs(keys, run_off, k):

@@ -95,7 +95,36 @@ ORC_PAIR_CMP(pair_cmp_f32, ORC_F32)
 ORC_PAIR_CMP(pair_cmp_bf16, ORC_BF16)
 ORC_PAIR_CMP(pair_cmp_u64, ORC_U64)
 
+/* The largest first: values descending, equal values by ascending index. */
+#define ORC_PAIR_CMP_DESC(name, dt)                                      \
+    static int name(const void *pa, const void *pb)                     \
+    {                                                                    \
+        const orc_pair *x = (const orc_pair *)pa;                        \
+        const orc_pair *y = (const orc_pair *)pb;                        \
+        int c = oracle_key_cmp(dt, y->key, x->key);                      \
+        if (c != 0)                                                      \
+            return c;                                                    \
+        return cmp_unsigned(x->idx, y->idx);                             \
+    }
+ORC_PAIR_CMP_DESC(pair_cmp_desc_u32, ORC_U32)
+ORC_PAIR_CMP_DESC(pair_cmp_desc_i32, ORC_I32)
+ORC_PAIR_CMP_DESC(pair_cmp_desc_f32, ORC_F32)
+ORC_PAIR_CMP_DESC(pair_cmp_desc_bf16, ORC_BF16)
+ORC_PAIR_CMP_DESC(pair_cmp_desc_u64, ORC_U64)
+
 typedef int (*orc_cmp_fn)(const void *, const void *);
+
+static orc_cmp_fn pair_cmp_desc_for(int dtype)
+{
+    switch (dtype) {
+    case ORC_U32: return pair_cmp_desc_u32;
+    case ORC_I32: return pair_cmp_desc_i32;
+    case ORC_F32: return pair_cmp_desc_f32;
+    case ORC_BF16: return pair_cmp_desc_bf16;
+    case ORC_U64: return pair_cmp_desc_u64;
+    default: return 0;
+    }
+}
 
 static orc_cmp_fn pair_cmp_for(int dtype)
 {
@@ -166,6 +195,29 @@ int oracle_select(const void *keys, uint64_t n, int dtype, uint64_t k,
     for (i = 0; i < k; ++i)             /* ranks 1..k */
         sel_idx[i] = (uint32_t)v[i].idx;
     *kth_idx = (uint32_t)v[k - 1].idx;  /* the object of rank k */
+    free(v);
+    return 0;
+}
+
+int oracle_select_largest(const void *keys, uint64_t n, int dtype, uint64_t k,
+                          uint32_t *sel_idx, uint32_t *kth_idx)
+{
+    orc_cmp_fn cmp = pair_cmp_desc_for(dtype);
+    orc_pair *v;
+    uint64_t i;
+    if (!keys || !sel_idx || !kth_idx || !cmp || k < 1 || k > n || n > 0xffffffffull)
+        return -1;
+    v = (orc_pair *)malloc(n * sizeof(orc_pair));
+    if (!v)
+        return -1;
+    for (i = 0; i < n; ++i) {
+        v[i].key = load_key(keys, i, dtype);
+        v[i].idx = i;
+    }
+    qsort(v, (size_t)n, sizeof(orc_pair), cmp);
+    for (i = 0; i < k; ++i)
+        sel_idx[i] = (uint32_t)v[i].idx;
+    *kth_idx = sel_idx[k - 1]; /* the pair of rank k in this order */
     free(v);
     return 0;
 }

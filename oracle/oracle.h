@@ -50,6 +50,12 @@ int oracle_key_cmp(int dtype, uint64_t a, uint64_t b);
  * Returns 0, or -1 on bad arguments / allocation failure. */
 int oracle_sort_order(const void *keys, uint64_t n, int dtype, uint32_t *perm);
 
+/* The k largest: pairs ordered by value descending, equal values by
+ * ascending index (the position tie-break of Section 2 kept), first k taken.
+ * Arguments and returns as oracle_select. */
+int oracle_select_largest(const void *keys, uint64_t n, int dtype, uint64_t k,
+                          uint32_t *sel_idx, uint32_t *kth_idx);
+
 /* The k smallest pairs.  sel_idx receives their k indices in ascending pair
  * order; *kth_idx the index of the pair of rank k.  Needs 1 <= k <= n,
  * n < 2^32.  Returns 0, or -1 on bad arguments. */

@@ -25,6 +25,7 @@ TOPK_FLAG_CHECK_SORTED = 0x1
 TOPK_FLAG_RAW_DELTA = 0x2
 TOPK_FLAG_TINY_CAND = 0x4
 TOPK_FLAG_NO_BULK_COPY = 0x8
+TOPK_FLAG_LARGEST = 0x10
 
 DTYPE_NAMES = {TOPK_U32: "u32", TOPK_I32: "i32", TOPK_F32: "f32", TOPK_BF16: "bf16",
                TOPK_U64: "u64"}

@@ -24,6 +24,9 @@ typedef uint64_t u64;
 typedef unsigned __int128 u128;
 
 enum : int { DT_U32 = 0, DT_I32 = 1, DT_F32 = 2, DT_BF16 = 3, DT_U64 = 4 };
+// DT_DESC + DT: the same key type ordered the other way (selection of the k
+// largest); ties are still broken by the smaller position.
+constexpr int DT_DESC = 8;
 
 // ---------------------------------------------------------------- key maps
 
@@ -73,6 +76,19 @@ template <> struct Key<DT_U64> {
     static constexpr int KW = 64;
     __host__ __device__ static key_t fwd(raw_t x) { return x; }
     __host__ __device__ static raw_t inv(key_t k) { return k; }
+};
+
+// Descending order: the ascending key image complemented within its width
+// (16 bits for bf16), so the k smallest images are the k largest keys.
+template <int DT> struct Key {
+    static_assert(DT >= DT_DESC && DT < DT_DESC + 5, "descending key codes only");
+    typedef Key<DT - DT_DESC> A;
+    typedef typename A::raw_t raw_t;
+    typedef typename A::key_t key_t;
+    static constexpr int KW = A::KW;
+    static constexpr key_t FLIP = (DT - DT_DESC == DT_BF16) ? (key_t)0xFFFFu : (key_t)~(key_t)0;
+    __host__ __device__ static key_t fwd(raw_t x) { return A::fwd(x) ^ FLIP; }
+    __host__ __device__ static raw_t inv(key_t k) { return A::inv(k ^ FLIP); }
 };
 
 // ------------------------------------------------------------- composites
@@ -201,8 +217,9 @@ struct SelArgs {
 // every composite of that type is at or below it, and the window histogram
 // spreads over the key bits actually used (16 for bf16).
 template <int DT> __host__ __device__ inline u128 key_domain_max() {
-    return DT == DT_U64 ? (((u128)~(u64)0) << 32) | 0xFFFFFFFFu
-                        : (((u128)(DT == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu)) << 32) | 0xFFFFFFFFu;
+    constexpr int B = DT % DT_DESC;
+    return B == DT_U64 ? (((u128)~(u64)0) << 32) | 0xFFFFFFFFu
+                       : (((u128)(B == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu)) << 32) | 0xFFFFFFFFu;
 }
 
 // Histogram of a window [lo, hi]: bin = (c - lo) >> sh with the shift chosen

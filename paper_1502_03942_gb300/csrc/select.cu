@@ -1194,6 +1194,16 @@ topk_status topk_select(topk_ctx* ctx, const void* d_keys, uint64_t n, uint64_t 
     if (reinterpret_cast<uintptr_t>(d_out_keys) % (uintptr_t)w) return TOPK_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (params && (params->flags & TOPK_FLAG_LARGEST)) {
+        switch (dtype) {
+        case TOPK_U32: return run_select<DT_DESC + DT_U32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+        case TOPK_I32: return run_select<DT_DESC + DT_I32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+        case TOPK_F32: return run_select<DT_DESC + DT_F32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+        case TOPK_BF16: return run_select<DT_DESC + DT_BF16>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+        case TOPK_U64: return run_select<DT_DESC + DT_U64>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
+        default: return TOPK_EINVAL;
+        }
+    }
     switch (dtype) {
     case TOPK_U32: return run_select<DT_U32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);
     case TOPK_I32: return run_select<DT_I32>(ctx, d_keys, n, k, d_out_keys, d_out_idx, d_kth_key, d_kth_idx, params, st);

@@ -77,26 +77,29 @@ def expected_by_brute_force(keys, dtype, k):
 
 # ------------------------------------------------------------------ checks
 
+def random_bits(g, dtype, n):
+    """n keys drawn from a small pool per type, so that ties, -0/+0, NaNs and
+    the signed/unsigned difference all occur."""
+    if dtype in ("f32", "bf16"):
+        pool = [0x00000000, 0x80000000, 0x3F800000, 0xBF800000, 0x7F800000,
+                0xFF800000, 0x7FC00000, 0xFFC00000, 0x00000001, 0x80000001]
+        if dtype == "bf16":
+            pool = [p >> 16 for p in pool] + [0x0001, 0x8001]
+        return np.array(g.choice(pool, size=n), dtype=STORE[dtype])
+    if dtype == "u64":
+        pool = [0, 1, 1 << 32, (1 << 63) - 1, 1 << 63, (1 << 64) - 1]
+        return np.array([pool[i] for i in g.integers(0, len(pool), size=n)], dtype=np.uint64)
+    # the same pool for u32 and i32: the two orders differ on it
+    pool = [0, 1, 2, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFE, 0xFFFFFFFF]
+    return np.array(g.choice(pool, size=n), dtype=np.uint32)
+
+
 def check_brute_force(orc, seed=0, sizes=(1, 2, 3, 5, 8, 13, 31, 64)):
     fails = []
     g = np.random.Generator(np.random.Philox(seed))
     for dtype in ("u32", "i32", "f32", "bf16", "u64"):
         for n in sizes:
-            if dtype in ("f32", "bf16"):
-                # small value pool with specials so ties and -0/+0/NaN occur
-                pool = [0x00000000, 0x80000000, 0x3F800000, 0xBF800000, 0x7F800000,
-                        0xFF800000, 0x7FC00000, 0xFFC00000, 0x00000001, 0x80000001]
-                if dtype == "bf16":
-                    pool = [p >> 16 for p in pool] + [0x0001, 0x8001]
-                keys = np.array(g.choice(pool, size=n), dtype=STORE[dtype])
-            elif dtype == "u64":
-                pool = [0, 1, 1 << 32, (1 << 63) - 1, 1 << 63, (1 << 64) - 1]
-                keys = np.array([pool[i] for i in g.integers(0, len(pool), size=n)],
-                                dtype=np.uint64)
-            else:
-                # the same pool for u32 and i32: the two orders differ on it
-                pool = [0, 1, 2, 0x7FFFFFFF, 0x80000000, 0xFFFFFFFE, 0xFFFFFFFF]
-                keys = np.array(g.choice(pool, size=n), dtype=np.uint32)
+            keys = random_bits(g, dtype, n)
             for k in range(1, n + 1):
                 want_sel, want_kth = expected_by_brute_force(keys, dtype, k)
                 sel, kth = orc.select(keys, dtype, k)
@@ -276,6 +279,40 @@ def check_delete_min_vs_heap(orc, seed=5):
     return fails
 
 
+def check_largest_brute_force(orc, seed=8):
+    """The k largest against brute force (values descending by Python's own
+    int/float order, equal values by ascending position) for every key type,
+    and against the k smallest of the complemented u32 / u64 keys."""
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for dtype in ("u32", "i32", "f32", "bf16", "u64"):
+        vk = VALUE_KEY[dtype]
+        for n in (1, 2, 5, 13, 40):
+            bits = random_bits(g, dtype, n)
+            order = sorted(range(n), key=lambda i: (_neg(vk(int(bits[i]))), i))
+            for k in sorted({1, n // 2 + 1, n}):
+                sel, kth = orc.select_largest(bits, dtype, k)
+                if list(sel) != order[:k] or kth != order[k - 1]:
+                    fails.append(f"largest {dtype} n={n} k={k}")
+    for dtype, top in (("u32", 0xFFFFFFFF), ("u64", 0xFFFFFFFFFFFFFFFF)):
+        store = np.uint32 if dtype == "u32" else np.uint64
+        bits = g.integers(0, 8, size=500).astype(store)
+        comp = (np.array(top, dtype=store) - bits).astype(store)
+        for k in (1, 100, 500):
+            sel, kth = orc.select_largest(bits, dtype, k)
+            want, wkth = orc.select(comp, dtype, k)
+            if list(sel) != list(want) or kth != wkth:
+                fails.append(f"largest vs complemented smallest {dtype} k={k}")
+    return fails
+
+
+def _neg(v):
+    """Reverses a value key's order (a float or int, or a NaN's tuple key)."""
+    if isinstance(v, tuple):
+        return tuple(-x if isinstance(x, (int, float)) else x for x in v)
+    return -v
+
+
 # ---- top-k most frequent objects (Section 7) ----
 
 def load_kat():
@@ -442,4 +479,4 @@ ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_ca
               check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
               check_batched_rows, check_delete_min_vs_heap, check_philox_kat,
               check_pac_worked_example, check_frequent_vs_counter, check_bernoulli_decisions,
-              check_frequent_plan]
+              check_frequent_plan, check_largest_brute_force]

@@ -14,8 +14,8 @@ from oracle import build as obuild
 import _pins
 
 MUTATIONS = {
-    "tiebreak_reversed": ("return cmp_unsigned(x->idx, y->idx);",
-                          "return cmp_unsigned(y->idx, x->idx);"),
+    "tiebreak_reversed": ("return cmp_unsigned(x->idx, y->idx); /* Section 2 tie-break */",
+                          "return cmp_unsigned(y->idx, x->idx); /* Section 2 tie-break */"),
     "negatives_ascending": ("return cmp_unsigned(mag_b, mag_a);     /* negatives",
                             "return cmp_unsigned(mag_a, mag_b);     /* negatives"),
     "sign_rule_flipped": ("return neg_a ? -1 : 1;", "return neg_a ? 1 : -1;"),
@@ -34,6 +34,8 @@ MUTATIONS = {
     "ec_counts_sample_only": ("            freq[lo].count += 1;", "            freq[lo].count += mask[i];"),
     "philox_lanes_swapped": ("        c1 = lo1;\n", "        c1 = lo0;\n"),
     "pac_rate_first_term_only": ("rho_n = 4.0 / (eps * eps) * (a > b ? a : b);", "rho_n = 4.0 / (eps * eps) * a;"),
+    "largest_ties_reversed": ("        return cmp_unsigned(x->idx, y->idx);                             \\\n",
+                              "        return cmp_unsigned(y->idx, x->idx);                             \\\n"),
     "take_k_minus_one": ("for (i = 0; i < k; ++i)             /* ranks 1..k */",
                          "for (i = 1; i < k; ++i)             /* ranks 1..k */"),
 }

@@ -206,3 +206,53 @@ def test_philox_known_answers(tk):
         ctr, key, want = vals[0:4], vals[4:6], vals[6:10]
         got = bits_of(tk.topk_debug_philox(ctr, key, 1))
         assert [int(x) for x in got] == want
+
+
+# ---- the k largest (TOPK_FLAG_LARGEST) ----
+
+def check_largest(keys_bits, name, k, out, orc):
+    ok, oi, kk, ki = out
+    got_idx = bits_of(oi)
+    want_sel, want_kth = orc.select_largest(keys_bits, name, k)
+    assert got_idx.size == k
+    assert np.array_equal(np.sort(got_idx), np.sort(want_sel)), "selected set differs"
+    assert np.array_equal(bits_of(ok), keys_bits[got_idx]), "output keys are not the input keys"
+    assert int(bits_of(ki)[0]) == want_kth, "rank-k position differs"
+    assert int(bits_of(kk)[0]) == int(keys_bits[want_kth]), "rank-k key differs"
+
+
+@pytest.mark.parametrize("name", ["u32", "i32", "f32", "bf16", "u64"])
+@pytest.mark.parametrize("n", [1, 7, 4096, 70001, 300007])
+def test_largest_sizes_and_ks(tk, ctx, orc, name, n):
+    keys = keys_for(name, n, seed=n + 11)
+    d = to_device(keys, name)
+    p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
+    for k in ks_for(n):
+        check_largest(keys, name, k, tk.topk_select(ctx, d, k, params=p), orc)
+
+
+@pytest.mark.parametrize("name", ["u32", "f32", "bf16", "u64"])
+def test_largest_heavy_ties_and_specials(tk, ctx, orc, name):
+    keys = keys_for(name, 200003, seed=13, kind="ties")
+    d = to_device(keys, name)
+    p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
+    for k in ks_for(200003):
+        check_largest(keys, name, k, tk.topk_select(ctx, d, k, params=p), orc)
+
+
+def test_largest_full_size_properties(tk, ctx, orc):
+    """n = 2^28 f32 N(0,1) keys, the 1024 and the n/2 largest: every selected
+    key is at or above the rank-k key, the rest at or below it, ties split by
+    position, the count of keys above it below k (checked with torch)."""
+    import torch
+    n = 1 << 28
+    d = wl.device_f32_dataset("normal", n, seed=31)
+    p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
+    for k in (1024, n // 2):
+        ok, oi, kk, ki = tk.topk_select(ctx, d, k, params=p)
+        kth = kk.view(torch.float32)[0]
+        assert torch.all(d[oi.view(torch.int32).long()] >= kth)
+        above = int((d > kth).sum().item())
+        equal_before = int(((d == kth) & (torch.arange(n, device=d.device) <= ki.view(torch.int32)[0].long())).sum().item())
+        assert above + equal_before == k
+        assert int(torch.unique(oi.view(torch.int32)).numel()) == k

@@ -133,6 +133,15 @@ topk_status topk_select(topk_ctx *ctx, const void *d_keys, uint64_t n, uint64_t 
                         void *d_kth_key, uint32_t *d_kth_idx,
                         const topk_params *params, void *stream);
 
+/* The key of rank k alone (Section 4: the problem asks for the k smallest
+ * or for the element of rank k): topk_select whose selected set is formed
+ * in context-owned device memory (k keys and k uint32 positions, grown on
+ * demand; growing waits for the device) and not returned.  Arguments,
+ * flags (TOPK_FLAG_LARGEST: the k-th largest) and errors as topk_select. */
+topk_status topk_select_kth(topk_ctx *ctx, const void *d_keys, uint64_t n, uint64_t k,
+                            topk_dtype dtype, void *d_kth_key, uint32_t *d_kth_idx,
+                            const topk_params *params, void *stream);
+
 /* Multisequence selection over p locally sorted runs (Section 4.2;
  * Appendix A, Algorithm msSelect, with several pivots per round as in
  * Section 4.3 "Multiple Concurrent Trials").

@@ -102,6 +102,9 @@ def load_library(path: str = LIB_PATH):
     if hasattr(lib, "topk_select_sorted_runs_flexible"):
         lib.topk_select_sorted_runs_flexible.argtypes = [vp, vp, vp, u32, u64, u64, i32, vp, vp, vp, vp, vp, vp, vp]
         lib.topk_select_sorted_runs_flexible.restype = st
+    if hasattr(lib, "topk_select_kth"):
+        lib.topk_select_kth.argtypes = [vp, vp, u64, u64, i32, vp, vp, vp, vp]
+        lib.topk_select_kth.restype = st
     if hasattr(lib, "topk_frequent"):
         lib.topk_frequent_plan.argtypes = [u64, ctypes.POINTER(topk_freq_params), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(u32)]
@@ -384,6 +387,25 @@ def topk_runs_delete_min_flexible(ctx: Context, keys, run_off, cursor, kmin: int
     _check(st, "topk_runs_delete_min_flexible")
     if check:
         _check(ctx.sync(stream), "topk_runs_delete_min_flexible (device)")
+    return out
+
+
+def topk_select_kth(ctx: Context, keys, k: int, params: topk_params | None = None, stream=None, out=None,
+                    check: bool = True):
+    """The key of rank k and its position (the k-th smallest, or the k-th
+    largest with TOPK_FLAG_LARGEST); the selected set stays in the context.
+    Returns (kth_key[1] of the key dtype, kth_idx[1] uint32)."""
+    torch = _torch()
+    if out is None:
+        out = (torch.empty(1, dtype=keys.dtype, device=keys.device),
+               torch.empty(1, dtype=torch.uint32, device=keys.device))
+    kk, ki = out
+    st = load_library().topk_select_kth(ctx.handle, _ptr(keys), keys.numel(), int(k), dtype_code(keys), _ptr(kk),
+                                        _ptr(ki), ctypes.byref(params) if params is not None else None,
+                                        _stream_ptr(stream))
+    _check(st, "topk_select_kth")
+    if check:
+        _check(ctx.sync(stream), "topk_select_kth (device)")
     return out
 
 

@@ -177,6 +177,7 @@ void topk_ctx_destroy(topk_ctx* ctx) {
             if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
     if (ctx->scratch.base) cudaFree(ctx->scratch.base);
     if (ctx->freq.base) cudaFree(ctx->freq.base);
+    if (ctx->aux.base) cudaFree(ctx->aux.base);
     if (ctx->d_err) cudaFree(ctx->d_err);
     delete ctx;
 }

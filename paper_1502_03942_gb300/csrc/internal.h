@@ -37,6 +37,7 @@ struct topk_ctx {
     int sms = 0;
     topk::Scratch scratch;
     topk::Scratch freq;            // top-k most frequent objects: hash table and candidates
+    topk::Scratch aux;             // outputs that a call forms but does not return (topk_select_kth)
     uint32_t* d_err = nullptr;     // first device error (latched), own allocation
     uint32_t* d_counter = nullptr; // last-block-done counters (zero between calls)
     void* d_state = nullptr;       // selection state (SelState or RunsState)

@@ -1214,6 +1214,36 @@ topk_status topk_select(topk_ctx* ctx, const void* d_keys, uint64_t n, uint64_t 
     }
 }
 
+topk_status topk_select_kth(topk_ctx* ctx, const void* d_keys, uint64_t n, uint64_t k, topk_dtype dtype,
+                            void* d_kth_key, uint32_t* d_kth_idx, const topk_params* params, void* stream) {
+    if (!ctx || !d_keys || !d_kth_key || !d_kth_idx) return TOPK_EINVAL;
+    const int w = dtype_bytes(dtype);
+    if (w == 0) return TOPK_EINVAL;
+    if (k < 1 || k > n || n > 0xFFFFFFFFull) return TOPK_EINVAL;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
+    // the selected set goes to context-owned memory
+    const size_t key_bytes = ((size_t)k * w + 255) & ~(size_t)255;
+    const size_t need = key_bytes + (size_t)k * 4;
+    Scratch& s = ctx->aux;
+    if (s.bytes < need) {
+        if (s.base) {
+            if (cudaDeviceSynchronize() != cudaSuccess) return TOPK_ECUDA;
+            cudaFree(s.base);
+            s.base = nullptr;
+            s.bytes = 0;
+        }
+        if (cudaMalloc(&s.base, need) != cudaSuccess) {
+            cudaGetLastError();
+            s.base = nullptr;
+            return TOPK_ENOMEM;
+        }
+        s.bytes = need;
+    }
+    char* base = static_cast<char*>(s.base);
+    return topk_select(ctx, d_keys, n, k, dtype, base, reinterpret_cast<uint32_t*>(base + key_bytes), d_kth_key,
+                       d_kth_idx, params, stream);
+}
+
 topk_status topk_select_noalloc(const void* d_keys, uint64_t n, uint64_t k, topk_dtype dtype,
                                 void* d_out_keys, uint32_t* d_out_idx, void* d_kth_key,
                                 uint32_t* d_kth_idx, uint32_t* d_status, void* stream) {

@@ -715,6 +715,24 @@ def run_probe(spec):
     return 0
 
 
+def run_probe_frequent(spec):
+    """Top-k most frequent objects for profilers: ALG:LOG2N (ALG ec or pac;
+    Zipf objects, k = 32, eps = 3e-4, delta = 1e-4), two calls."""
+    import torch
+    import paper_1502_03942_gb300 as tk
+    from paper_1502_03942_gb300 import workloads as wl
+    alg, log2n = spec.split(":")
+    ctx = tk.Context(0)
+    x = wl.device_zipf_objects(1 << int(log2n), seed=2024)
+    fp = tk.make_freq_params(32, algorithm=tk.TOPK_FREQ_EC if alg == "ec" else tk.TOPK_FREQ_PAC,
+                             epsilon=3e-4, delta=1e-4, seed=3)
+    out = tk.topk_frequent(ctx, x, fp)
+    tk.topk_frequent(ctx, x, fp, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe_frequent": spec, "sample_size": int(out[2].view(torch.int64).item())}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -726,7 +744,11 @@ def main():
                     help="skip the plain, batched, sorted-runs and served measurements")
     ap.add_argument("--probe", default=None,
                     help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
+    ap.add_argument("--probe-frequent", default=None,
+                    help="profiling aid: ALG:LOG2N, two calls of topk_frequent (ec or pac)")
     args = ap.parse_args()
+    if args.probe_frequent:
+        return run_probe_frequent(args.probe_frequent)
     if args.impl == "reference":
         return run_reference(args)
     import __graft_entry__

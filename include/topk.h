@@ -277,7 +277,10 @@ typedef struct {
     uint64_t seed;         /* Philox4x32-10 key of the sample decisions */
     uint64_t max_distinct; /* most distinct sampled objects the hash table
                               must hold (it has the next power of two above
-                              twice this many slots, 8 bytes each); 0 = 2^22 */
+                              twice this many slots, 8 bytes each); 0 = 2^22;
+                              lowered to a bound on the sample size (its
+                              mean plus eight standard deviations plus 1024,
+                              at most n) */
 } topk_freq_params;
 
 /* Sampling probability rho and k* that topk_frequent would use for n

@@ -491,7 +491,13 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
     if (rs != TOPK_OK) return rs;
     const bool ec = fp->algorithm == TOPK_FREQ_EC;
     if (ec && kstar > FQ_EXACT_MAX) return TOPK_EINVAL;
-    const u64 distinct = fp->max_distinct ? fp->max_distinct : FQ_DEFAULT_DISTINCT;
+    // distinct sampled objects are at most the sample size: bound it far
+    // above its mean (a larger sample has negligible probability and would
+    // only be reported as TOPK_ENOMEM) and by n
+    const double mean = rho * (double)n;
+    const u64 sample_bound = std::min<u64>(n, (u64)std::ceil(mean + 8.0 * std::sqrt(mean) + 1024.0));
+    const u64 distinct =
+        std::min<u64>(fp->max_distinct ? fp->max_distinct : FQ_DEFAULT_DISTINCT, sample_bound);
     const u32 log_cap = std::max<u32>(12, ceil_log2(2 * std::max<u64>(distinct, (u64)kstar)));
     if (log_cap > 31) return TOPK_EINVAL;
     const u64 cap = 1ull << log_cap;

@@ -313,7 +313,8 @@ topk_status topk_frequent_plan(uint64_t n, const topk_freq_params *fp, double *r
  * topk_frequent_plan, plus k* > 4096 for EC and a NULL pointer).  Reported
  * by topk_status_sync(): TOPK_EINVAL when fewer than k (PAC) or k* (EC)
  * distinct objects were sampled, TOPK_ENOMEM when more distinct objects
- * were sampled than the table holds (raise max_distinct). */
+ * were sampled than the table holds (raise max_distinct; an overfilled
+ * table ends the call in bounded time, its counts then undefined). */
 topk_status topk_frequent(topk_ctx *ctx, const void *d_objects, uint64_t n, topk_dtype dtype,
                           const topk_freq_params *fp, uint32_t *d_out_obj,
                           uint64_t *d_out_count, uint64_t *d_sample_size, void *stream);

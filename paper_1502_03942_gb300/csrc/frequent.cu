@@ -44,10 +44,17 @@ __host__ __device__ __forceinline__ u32 fq_mix(u32 x) {
 __device__ __forceinline__ u64 fq_word(u32 obj, u32 count) { return ((u64)(0xFFFFFFFFu - count) << 32) | obj; }
 
 // Adds `c` occurrences of `obj` to the HBM table (linear probing from the
-// hash's low bits).  False when the table has no free slot left.
+// hash's low bits).  False when neither the object nor a free slot turns up
+// within FQ_TABLE_PROBES slots: the table holds more distinct objects than
+// it was sized for (at the load it is sized for, at most one half, a probe
+// sequence that long does not occur), so a call that overfills it ends in
+// bounded time with TOPK_ENOMEM.
+constexpr u32 FQ_TABLE_PROBES = 4096;
+
 __device__ bool fq_table_add(u64* table, u32 mask, u32 obj, u32 c) {
     u32 h = fq_mix(obj) & mask;
-    for (u32 probe = 0; probe <= mask; ++probe) {
+    const u32 limit = mask < FQ_TABLE_PROBES ? mask + 1 : FQ_TABLE_PROBES;
+    for (u32 probe = 0; probe < limit; ++probe) {
         u64* s = table + h;
         u64 w = __ldcg(s);
         if (w == FQ_EMPTY) {
@@ -242,7 +249,7 @@ __global__ void __launch_bounds__(FQ_NT, 3) k_freq_count(FreqArgs a) {
     u32 sampled = 0;
     for (u64 t = blockIdx.x; t < tiles; t += gridDim.x) {
         const u64 q0 = t * tile_quads + threadIdx.x;
-        if (t < full_tiles) sampled += fq_tile<ALL, true, VEC>(L, a, q0, queue, lane);
+        if (VEC && t < full_tiles) sampled += fq_tile<ALL, true, VEC>(L, a, q0, queue, lane);
         else sampled += fq_tile<ALL, false, VEC>(L, a, q0, queue, lane);
     }
     __syncthreads();
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(FQ_NT, 3) k_freq_exact(ExactArgs a) {
     for (u64 t = blockIdx.x; t * tile_quads < quads; t += gridDim.x) {
         const u64 q0 = t * tile_quads + threadIdx.x;
         uint4 x[FQ_XQUADS];
-        if (t < full_tiles) {
+        if (VEC && t < full_tiles) {
 #pragma unroll
             for (int j = 0; j < FQ_XQUADS; ++j) x[j] = ld_stream(reinterpret_cast<const uint4*>(a.obj) + q0 + j * FQ_NT);
 #pragma unroll

@@ -66,11 +66,13 @@ typedef enum {
                                         the overflow paths run */
 #define TOPK_FLAG_NO_BULK_COPY 0x8u  /* first pass: per-thread vector loads
                                         instead of the bulk-copy pipeline */
-#define TOPK_FLAG_LARGEST 0x10u      /* topk_select: the k largest keys
-                                        instead of the k smallest (equal
-                                        keys still by the smaller position);
-                                        the rank-k key is the smallest
-                                        selected one */
+#define TOPK_FLAG_LARGEST 0x10u      /* topk_select, topk_select_kth: the
+                                        k largest keys instead of the k
+                                        smallest (equal keys still by the
+                                        smaller position); the rank-k key is
+                                        the smallest selected one.  The
+                                        batched, tuning and sorted-runs calls
+                                        return TOPK_EINVAL for it */
 
 /* Tuning knobs; a zero field means "choose automatically".  None of them can
  * change a result, only the time taken. */

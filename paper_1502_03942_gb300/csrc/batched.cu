@@ -374,6 +374,7 @@ extern "C" topk_status topk_select_batched(topk_ctx* ctx, const void* d_keys, co
     if (!batch_ptrs_ok(ctx, d_keys, d_row_off, d_row_k, rows, dtype, d_out_keys, d_out_idx, d_out_off, d_kth_keys,
                        d_kth_idx))
         return TOPK_EINVAL;
+    if (params && (params->flags & TOPK_FLAG_LARGEST)) return TOPK_EINVAL; // k smallest only
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     topk_params p{};
     if (params) p = *params;
@@ -400,6 +401,7 @@ extern "C" topk_status topk_tune_batched(topk_ctx* ctx, const void* d_keys, cons
     if (!batch_ptrs_ok(ctx, d_keys, d_row_off, d_row_k, rows, dtype, d_out_keys, d_out_idx, d_out_off, d_kth_keys,
                        d_kth_idx))
         return TOPK_EINVAL;
+    if (base && (base->flags & TOPK_FLAG_LARGEST)) return TOPK_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     topk_params b0{};

@@ -615,6 +615,7 @@ static topk_status run_sorted_runs(topk_ctx* ctx, const void* d_keys, const uint
     if (flexible && (!d_k || kmin == 0 || kmin > kmax || kmax > 0xFFFFFFFFull)) return TOPK_EINVAL;
     if (!flexible && (k == 0 || k > 0xFFFFFFFFull)) return TOPK_EINVAL;
     if (dtype != TOPK_U64 || p == 0 || p > (1u << 24)) return TOPK_EINVAL;
+    if (params && (params->flags & TOPK_FLAG_LARGEST)) return TOPK_EINVAL; // ascending runs only
     if (reinterpret_cast<uintptr_t>(d_keys) % 8 || reinterpret_cast<uintptr_t>(d_run_off) % 8) return TOPK_EINVAL;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return TOPK_ECUDA;
     topk_params prm{};

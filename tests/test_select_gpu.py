@@ -257,18 +257,3 @@ def test_largest_full_size_properties(tk, ctx, orc):
         assert above + equal_before == k
         assert int(torch.unique(oi.view(torch.int32)).numel()) == k
 
-
-@pytest.mark.parametrize("name", ["u32", "f32", "bf16", "u64"])
-def test_kth_only(tk, ctx, orc, name):
-    """topk_select_kth: the rank-k key and position of the k smallest and of
-    the k largest, as the oracle's."""
-    n = 100003
-    keys = keys_for(name, n, seed=17, kind="ties" if name != "u64" else "uniform")
-    d = to_device(keys, name)
-    for k in (1, 1000, n // 2, n):
-        kk, ki = tk.topk_select_kth(ctx, d, k)
-        _, want = orc.select(keys, name, k)
-        assert int(bits_of(ki)[0]) == want and int(bits_of(kk)[0]) == int(keys[want])
-        kk, ki = tk.topk_select_kth(ctx, d, k, params=tk.make_params(flags=tk.TOPK_FLAG_LARGEST))
-        _, want = orc.select_largest(keys, name, k)
-        assert int(bits_of(ki)[0]) == want and int(bits_of(kk)[0]) == int(keys[want])

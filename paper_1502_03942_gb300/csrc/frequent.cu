@@ -6,7 +6,7 @@
 //
 // One GPU is one PE: the paper's distributed hash table is a single
 // open-addressing table in HBM, fed by block-local tables in shared memory
-// (the local aggregation of Lemma "topkapproxtime"); the selections are
+// (the local aggregation of Section 7.1's running-time lemma); the selections are
 // topk_select calls on the table itself.  A table slot is one 64-bit word
 // (0xFFFFFFFF - count) << 32 | object, so the table orders by count, larger
 // first, equal counts by the smaller object, and an empty slot
@@ -543,7 +543,7 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
         count_attr.fetch_or(dbit);
     }
 
-    // 1.-2. sample and count (Section 7.1)
+    // 1. sample and count (Section 7.1)
     cudaError_t e = cudaMemsetAsync(table, 0xFF, 8 * cap, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(cursor, 0, 8, st);
     if (e != cudaSuccess) return cuda_status(e);
@@ -569,7 +569,7 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
     if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx);
 
-    // 3. the `need` most frequently sampled objects: the smallest table words
+    // 2. the `need` most frequently sampled objects: the smallest table words
     rs = topk_select(ctx, table, cap, need, TOPK_U64, sel, sel_idx, kth, kth_idx, nullptr, stream);
     if (rs != TOPK_OK) return rs;
     if (!ec) {
@@ -579,7 +579,7 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
         count_launch(ctx);
         return cuda_status(e);
     }
-    // 4. EC: exact recount of the k* candidates (Section 7.2)
+    // 3. EC: exact recount of the k* candidates (Section 7.2)
     e = launch_dep(k_freq_check, 1, 32, 0, st, (const u64*)kth, ctx->d_err);
     u32* exact = reinterpret_cast<u32*>(base + o_exact);
     if (e == cudaSuccess) e = cudaMemsetAsync(exact, 0, 4ull * kstar, st);
@@ -621,7 +621,7 @@ topk_status topk_frequent(topk_ctx* ctx, const void* d_objects, uint64_t n, topk
                        kstar, comp);
     if (e != cudaSuccess) return cuda_status(e);
     count_launch(ctx, 3);
-    // 5. the k most frequent candidates by exact count
+    // 4. the k most frequent candidates by exact count
     u64* sel2 = reinterpret_cast<u64*>(base + o_sel2);
     u32* idx2 = reinterpret_cast<u32*>(base + o_idx2);
     u64* kth2 = reinterpret_cast<u64*>(base + o_kth2);

@@ -57,6 +57,8 @@ class Oracle:
         lib.oracle_select.restype = i32
         lib.oracle_select_largest.argtypes = [vp, u64, i32, u64, vp, vp]
         lib.oracle_select_largest.restype = i32
+        lib.oracle_pairs_before.argtypes = [vp, u64, i32, u64, i32, vp]
+        lib.oracle_pairs_before.restype = i32
         lib.oracle_select_runs.argtypes = [vp, vp, u32, u64, vp, vp, vp]
         lib.oracle_select_runs.restype = i32
         lib.oracle_runs_delete_min.argtypes = [vp, vp, u32, vp, u64, vp, vp]
@@ -108,6 +110,16 @@ class Oracle:
                                           _ptr(kth)) != 0:
             raise ValueError("oracle_select_largest rejected its arguments")
         return sel[: int(k)], int(kth[0])
+
+    def pairs_before(self, keys: np.ndarray, dtype: str, pos: int, descending: bool = False) -> int:
+        """Number of pairs preceding (keys[pos], pos) in the ascending (or,
+        with ``descending``, the descending) value order, ties by position."""
+        a = _bits(keys, dtype)
+        c = np.zeros(1, np.uint64)
+        if self.lib.oracle_pairs_before(_ptr(a), a.size, DTYPE_CODES[dtype], int(pos),
+                                        1 if descending else 0, _ptr(c)) != 0:
+            raise ValueError("oracle_pairs_before rejected its arguments")
+        return int(c[0])
 
     def select_runs(self, keys: np.ndarray, run_off: np.ndarray, k: int):
         """(split[p], kth_run, kth_pos) for multisequence selection of rank k."""

@@ -222,6 +222,28 @@ int oracle_select_largest(const void *keys, uint64_t n, int dtype, uint64_t k,
     return 0;
 }
 
+/* The rank of one pair without sorting: the pairs (keys[i], i) that come
+ * before (keys[pos], pos) in the order of oracle_select (ascending values) or
+ * of oracle_select_largest (descending values), equal values by position.
+ * One comparison per element, straight from the definition of the order. */
+int oracle_pairs_before(const void *keys, uint64_t n, int dtype, uint64_t pos,
+                        int descending, uint64_t *count)
+{
+    uint64_t i, c = 0, v;
+    if (!keys || !count || !oracle_key_bytes(dtype) || pos >= n)
+        return -1;
+    v = load_key(keys, pos, dtype);
+    for (i = 0; i < n; ++i) {
+        int d = oracle_key_cmp(dtype, load_key(keys, i, dtype), v);
+        if (descending)
+            d = -d;
+        if (d < 0 || (d == 0 && i < pos))
+            ++c;
+    }
+    *count = c;
+    return 0;
+}
+
 /* The run r with run_off[r] <= g < run_off[r+1] (bisection over the
  * non-decreasing offsets; empty runs are skipped because their interval is
  * empty). */

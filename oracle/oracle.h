@@ -62,6 +62,14 @@ int oracle_select_largest(const void *keys, uint64_t n, int dtype, uint64_t k,
 int oracle_select(const void *keys, uint64_t n, int dtype, uint64_t k,
                   uint32_t *sel_idx, uint32_t *kth_idx);
 
+/* How many pairs (keys[i], i) precede the pair (keys[pos], pos): in the
+ * order of oracle_select when descending = 0, of oracle_select_largest when
+ * descending = 1.  The pair of rank k has k - 1 before it.  One pass over
+ * the keys, no sort (for checks at sizes where sorting is slow).  Returns 0,
+ * or -1 on bad arguments. */
+int oracle_pairs_before(const void *keys, uint64_t n, int dtype, uint64_t pos,
+                        int descending, uint64_t *count);
+
 /* Multisequence selection over p runs stored back to back in `keys`
  * (u64 keys; run r is keys[run_off[r] .. run_off[r+1]) ).  Pairs are ordered
  * by (key, run, position), i.e. by (key, concatenated index).  split[r]

@@ -454,7 +454,25 @@ def check_frequent_plan(orc):
     rho_big_p, ks_big_p = orc.frequent_plan(1 << 40, k, 1e-6, 1e-8, pes=1024, exact=True)
     if not ks_big_p > k:
         fails.append("EC k* grows with p")
+    # hand-evaluated closed forms (tests/golden/frequent_plan_values.txt):
+    # EC with p > 1 (so k* > k) and PAC where the first term of equation
+    # sampleSize is the larger one
+    for alg, n, kk, e, d, p, want_ks, want_rn in load_plan_values():
+        rho, ks = orc.frequent_plan(n, kk, e, d, pes=p, exact=(alg == "EC"))
+        if ks != want_ks or abs(rho * n / want_rn - 1) > 1e-12:
+            fails.append(f"{alg} plan n={n} k={kk} p={p}: k*={ks} rho*n={rho * n}")
     return fails
+
+
+def load_plan_values():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "frequent_plan_values.txt")):
+        line = line.split("#", 1)[0].split()
+        if not line:
+            continue
+        alg, n, k, eps, delta, p, ks, rn = line
+        rows.append((alg, int(n), int(k), float(eps), float(delta), int(p), int(ks), float(rn)))
+    return rows
 
 
 def check_batched_rows(orc, seed=4):
@@ -475,8 +493,32 @@ def check_batched_rows(orc, seed=4):
     return fails
 
 
+def check_pairs_before(orc, seed=9):
+    """The one-pass rank count against brute force with Python's own value
+    order, both directions, on inputs full of ties: the pair of rank r has
+    r - 1 pairs before it (Section 2 order on (value, position))."""
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for dtype in ("u32", "i32", "f32", "bf16", "u64"):
+        for n in (1, 2, 9, 40):
+            keys = random_bits(g, dtype, n)
+            vk = VALUE_KEY[dtype]
+            for pos in range(n):
+                asc = sum(1 for j in range(n)
+                          if (vk(int(keys[j])), j) < (vk(int(keys[pos])), pos))
+                desc = sum(1 for j in range(n)
+                           if (_neg(vk(int(keys[j]))), j) < (_neg(vk(int(keys[pos]))), pos))
+                if orc.pairs_before(keys, dtype, pos) != asc:
+                    fails.append(f"pairs_before {dtype} n={n} pos={pos}")
+                    break
+                if orc.pairs_before(keys, dtype, pos, descending=True) != desc:
+                    fails.append(f"pairs_before descending {dtype} n={n} pos={pos}")
+                    break
+    return fails
+
+
 ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_cases,
               check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
               check_batched_rows, check_delete_min_vs_heap, check_philox_kat,
               check_pac_worked_example, check_frequent_vs_counter, check_bernoulli_decisions,
-              check_frequent_plan, check_largest_brute_force]
+              check_frequent_plan, check_largest_brute_force, check_pairs_before]

@@ -36,6 +36,13 @@ MUTATIONS = {
     "pac_rate_first_term_only": ("rho_n = 4.0 / (eps * eps) * (a > b ? a : b);", "rho_n = 4.0 / (eps * eps) * a;"),
     "largest_ties_reversed": ("        return cmp_unsigned(x->idx, y->idx);                             \\\n",
                               "        return cmp_unsigned(y->idx, x->idx);                             \\\n"),
+    "ec_natural_log_of_p": ("ks = sqrt(2.0 * log2((double)pes) / pes * log(n / delta)) / eps;",
+                            "ks = sqrt(2.0 * log((double)pes) / pes * log(n / delta)) / eps;"),
+    "ec_factor_two_dropped": ("ks = sqrt(2.0 * log2((double)pes) / pes * log(n / delta)) / eps;",
+                              "ks = sqrt(log2((double)pes) / pes * log(n / delta)) / eps;"),
+    "pac_first_term_2n": ("double a = 3.0 / k * log(4.0 * n / delta);",
+                          "double a = 3.0 / k * log(2.0 * n / delta);"),
+    "pairs_before_ties_inclusive": ("if (d < 0 || (d == 0 && i < pos))", "if (d < 0 || (d == 0 && i <= pos))"),
     "take_k_minus_one": ("for (i = 0; i < k; ++i)             /* ranks 1..k */",
                          "for (i = 1; i < k; ++i)             /* ranks 1..k */"),
 }

@@ -186,53 +186,146 @@ def algorithmic_bytes(k):
 
 # ------------------------------------------------------------------ oracle
 
-def time_oracle(budget_s=20.0, n_sample=1 << 22):
-    """The CPU oracle (sort-and-take, one thread) on a bounded sample: each
-    dataset's first n_sample keys, every k scaled to the sample."""
+def host_info():
+    """Host CPU: usable cores and model name (for the CPU baselines)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "cores": cores, "cpu_model": model or "unknown",
+            "arch": platform.machine()}
+
+
+def time_oracle(host_keys, budget_s=20.0, slice_n=1 << 22, threads=None):
+    """The CPU oracle as it stands (one full qsort of all pairs per selection)
+    on every host core: each thread runs oracle selections on its own
+    slice_n-key slice of one dataset's input (same bytes as the GPU arm),
+    every k of the workload scaled to the slice, until the budget is spent.
+    ctypes releases the GIL, so the threads' sorts run in parallel."""
+    import concurrent.futures as cf
     import numpy as np
     import oracle
-    from paper_1502_03942_gb300 import workloads as wl
     orc = oracle.default()
-    keys_done, t_total, calls = 0, 0.0, 0
+    info = host_info()
+    threads = threads or info["cores"]
+    items = []
+    for rep in range(64):
+        for ds in DATASETS:
+            x = host_keys[ds]
+            for k in KS:
+                kk = max(1, min(slice_n, k * slice_n // N if k > 1024 else k))
+                for t in range(threads):
+                    j = (rep * threads + t) % (x.size // slice_n)
+                    items.append((ds, j, kk))
+    t0 = time.perf_counter()
+    done = [0]
+
+    def work(item):
+        ds, j, kk = item
+        if time.perf_counter() - t0 > budget_s:
+            return 0
+        orc.select(host_keys[ds][j * slice_n:(j + 1) * slice_n], "f32", kk)
+        return slice_n
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        keys = sum(ex.map(work, items))
+    wall = time.perf_counter() - t0
+    calls = keys // slice_n
+    return {"value": keys / wall, "unit": "keys/s", "cores": threads, "kind": "oracle",
+            "cpu_model": info["cpu_model"], "nproc": info["nproc"], "arch": info["arch"],
+            "sample": f"{calls} oracle selections (full qsort of all pairs each), {threads} at a time, on "
+                      f"{slice_n}-key slices of the workload's own inputs (k scaled by slice/n above "
+                      f"1024), {wall:.1f} s wall"}
+
+
+def time_cpu_selection(host_keys):
+    """SURVEY-style CPU baselines on the full 2^28-key inputs: sort-and-take
+    on every host core (per-thread std::sort of one chunk, then a merge of
+    the chunks up to rank k), and std::nth_element on one core (normal
+    dataset).  Per selection: its own sort plus its merge."""
+    import numpy as np
+    import oracle
+    cb = oracle.cpu_baselines()
+    info = host_info()
+    th = info["cores"]
+    work = np.empty(N, np.uint64)
+    sel = np.empty(N // 2, np.uint32)
+    per, total = {}, 0.0
     for ds in DATASETS:
-        x = wl.f32_dataset(ds, n_sample, seed=2).view(np.uint32)
+        t0 = time.perf_counter()
+        cb.sort_chunks(host_keys[ds], th, work)
+        t_sort = time.perf_counter() - t0
         for k in KS:
-            kk = max(1, min(n_sample, k * n_sample // N if k > 1024 else k))
             t0 = time.perf_counter()
-            orc.select(x, "f32", kk)
-            t_total += time.perf_counter() - t0
-            keys_done += n_sample
-            calls += 1
-            if t_total > budget_s:
-                break
-        if t_total > budget_s:
-            break
-    return {"value": keys_done / t_total, "unit": "keys/s", "cores": 1, "kind": "oracle",
-            "sample": f"{calls} oracle selections on the first {n_sample} keys of each dataset "
-                      f"(k scaled by n_sample/n above 1024), {t_total:.1f} s of CPU"}
+            cb.take_k(work, th, k, sel)
+            t = t_sort + time.perf_counter() - t0
+            per[f"{ds}/k={k}"] = {"ms": 1e3 * t}
+            total += t
+    del work
+    nth, t_nth = {}, 0.0
+    w1 = np.empty(N, np.uint64)
+    for k in KS:
+        t0 = time.perf_counter()
+        cb.nth_element(host_keys["normal"], k, w1)
+        t = time.perf_counter() - t0
+        nth[f"normal/k={k}"] = {"ms": 1e3 * t}
+        t_nth += t
+    return {"sort_take": {"value": len(DATASETS) * len(KS) * N / total, "unit": "keys/s", "cores": th,
+                          "kind": "sort-and-take: per-thread std::sort of n/cores pairs + heap merge to rank k",
+                          "sample": "the full 2^28-key inputs of all 12 selections, one sort each",
+                          "per_case": per},
+            "nth_element": {"value": len(KS) * N / t_nth, "unit": "keys/s", "cores": 1,
+                            "kind": "std::nth_element on (key image, position) pairs, one core",
+                            "sample": "the full 2^28-key normal input, k in {1, 1024, 2^20, n/2}",
+                            "per_case": nth},
+            "cpu_model": info["cpu_model"], "nproc": info["nproc"], "arch": info["arch"]}
 
 
 def run_reference(args):
     rank = env_int("RANK", 0)
     if rank != 0:
         return 0
+    import numpy as np
+    from paper_1502_03942_gb300 import workloads as wl
+    info = host_info()
+    slice_n = 1 << 22
+    host_keys = {ds: wl.f32_dataset(ds, slice_n * info["cores"], seed=2).view(np.uint32) for ds in DATASETS}
     base = {"metric": METRIC, "unit": "keys/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "keys": "f32", "arm": "CPU oracle, 1 thread"}}
-    budget = max(5.0, 60.0 / max(1, args.steps + args.warmup))
+            "config": {"workload": WORKLOAD, "keys": "f32",
+                       "arm": f"CPU oracle on {info['cores']} host cores ({info['cpu_model']})"}}
+    budget = max(3.0, 60.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        time_oracle(budget_s=budget / 4, n_sample=1 << 20)
+        time_oracle(host_keys, budget_s=budget / 4, slice_n=1 << 20)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(time_oracle(budget_s=budget, n_sample=1 << 22))
+        vals.append(time_oracle(host_keys, budget_s=budget, slice_n=slice_n))
     wall = time.perf_counter() - t0
     v = statistics.median(r["value"] for r in vals)
     line = dict(base)
-    line.update({"value": v, "ms_per_step": 1e3 * wall / max(1, args.steps),
-                 "cpu_baseline": {"value": v, "unit": "keys/s", "cores": 1, "kind": "oracle",
-                                  "sample": vals[-1]["sample"]},
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line.update({"value": v, "ms_per_step": 1e3 * wall / max(1, args.steps), "cpu_baseline": cb,
                  "e2e": {"value": v, "unit": "keys/s", "h2d_bytes_per_step": 0,
                          "d2h_bytes_per_step": 0}})
     print(json.dumps(line), flush=True)
@@ -361,7 +454,10 @@ def measure_sorted_runs(tk, wl, torch, ctx):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3)}
+        tk.topk_select_sorted_runs(ctx, d_keys, d_off, k, out=out, check=True)
+        stt = ctx.last_stats()
+        res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3), "rounds_grid": stt["levels_grid"],
+                     "rounds_block": stt["levels_block"]}
     # flexible k (amsSelect): any k within 10% above the same targets
     for name, kmin in (("flex_k65536", 1 << 16), ("flex_half", total // 2)):
         kmax = kmin + kmin // 10
@@ -376,8 +472,11 @@ def measure_sorted_runs(tk, wl, torch, ctx):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        tk.topk_select_sorted_runs_flexible(ctx, d_keys, d_off, kmin, kmax, out=out, check=True)
+        stt = ctx.last_stats()
         res[name] = {"ms": ms, "keys_per_s": total / (ms / 1e3), "kmin": kmin, "kmax": kmax,
-                     "k": int(out[4].cpu().view(torch.int64)[0])}
+                     "k": int(out[4].cpu().view(torch.int64)[0]), "rounds_grid": stt["levels_grid"],
+                     "rounds_block": stt["levels_block"]}
     # bulk deleteMin* (Section 5): consecutive pops from cursors at 0
     d_cur = torch.zeros(1024, dtype=torch.uint64, device="cuda")
     for name, kmin, kmax in (("delete_min_k65536", 1 << 16, None), ("delete_min_flex_k65536", 1 << 16,
@@ -615,6 +714,34 @@ def run_ours(args):
     ctx.profile(False)
     ms = max_over_ranks(ms, dist, "cuda")
 
+    # per selection: each (dataset, k) call alone between CUDA events on the
+    # stream, the twelve calls interleaved, median over repetitions
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    reps = max(3, min(args.steps, 8))
+    evs = []
+    for _ in range(reps):
+        for ds in DATASETS:
+            for k in KS:
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                tk.topk_select(ctx, data[ds], k, params=params, out=outs[k], check=False, stream=stream)
+                a1.record(stream)
+                evs.append((ds, k, a0, a1))
+    torch.cuda.synchronize()
+    case_ms = {}
+    for ds, k, a0, a1 in evs:
+        case_ms.setdefault((ds, k), []).append(a0.elapsed_time(a1))
+    per_case = {}
+    for (ds, k), v in case_ms.items():
+        m = statistics.median(v)
+        gbs = algorithmic_bytes(k) / (m / 1e3) / 1e9
+        tk.topk_select(ctx, data[ds], k, params=params, out=outs[k], check=True, stream=stream)
+        stt = ctx.last_stats()
+        per_case[f"{ds}/k={k}"] = {"ms": m, "keys_per_s": N / (m / 1e3), "algorithmic_GBps": gbs,
+                                   "frac_of_hbm": gbs / peak, "grid_levels": stt["levels_grid"],
+                                   "first_candidates": stt["first_candidates"]}
+
     # end to end: pinned host input -> device, select, outputs -> host
     e2e = None
     if True:  # every rank: the timing is max-reduced across ranks
@@ -652,7 +779,6 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    peaks, peak_kind = measured_peaks()
     per_step = len(DATASETS) * len(KS)
     keys_per_s = world * args.steps * per_step * N / (ms / 1e3)
     alg_bytes = sum(algorithmic_bytes(k) for k in KS) * len(DATASETS)
@@ -660,7 +786,6 @@ def run_ours(args):
     pass_ms_avg = prof["pass_ms"] / max(1, prof["passes"])
     pass_alg = sum(N * 4 + (k * 8 if k == N // 2 else 0) for k in KS) / len(KS)
     achieved = pass_alg / (pass_ms_avg / 1e3) / 1e9
-    peak = float(peaks.get("hbm_gbs", 6800.0))
     line = {
         "metric": METRIC, "value": keys_per_s, "unit": "keys/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
@@ -675,6 +800,8 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_kind} hbm_gbs", "traffic": committed_traffic(),
                      "launch_ms_avg": pass_ms_avg, "algorithmic_bytes_per_launch": pass_alg},
+        "per_case": per_case,
+        "per_case_min_frac": min(v["frac_of_hbm"] for v in per_case.values()),
         "gpu_launches": int(prof["launches"]),
         "clocks": clocks.summary(),
         "e2e": e2e,
@@ -690,7 +817,10 @@ def run_ours(args):
             except Exception as e:  # reported in the line, never hides the main metric
                 line[key] = {"error": repr(e)}
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = time_oracle()
+        host_keys = {ds: data[ds].view(torch.int32).cpu().numpy().view("uint32") for ds in DATASETS}
+        line["cpu_baseline"] = time_oracle(host_keys)
+        line["cpu_selection"] = time_cpu_selection(host_keys)
+        del host_keys
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -95,8 +95,10 @@ typedef struct {
 /* Counters of the last completed call on a context (valid after
  * topk_status_sync). */
 typedef struct {
-    uint32_t levels_grid;      /* recursion levels run by the whole grid */
-    uint32_t levels_block;     /* recursion levels run inside one block */
+    uint32_t levels_grid;      /* recursion levels run by the whole grid; for the
+                                  sorted-runs calls, pivot rounds run by the grid */
+    uint32_t levels_block;     /* recursion levels (sorted runs: rounds) run
+                                  inside one block */
     uint32_t pivot_failures;   /* levels whose bracket missed rank k */
     uint32_t overflows;        /* levels whose candidates exceeded the buffer */
     uint64_t first_candidates; /* |b| after the first level */
@@ -352,26 +354,33 @@ topk_status topk_tuning_load(topk_ctx *ctx, const char *path);
 
 /* Selection without any allocation: the same computation and result as
  * topk_select, for callers that cannot allocate device memory at the point
- * of the call (no counterpart in the paper).  Such callers include code that
- * runs while a CUDA graph is being captured (cudaMalloc is not permitted
- * then), code inside another framework's allocator or memory-pool callbacks,
- * and latency-critical paths that cannot accept the device-wide
- * synchronisation that cudaMalloc / cudaFree may cause.  The library's
- * scratch for this call (about 6 MiB: state, counters and candidate buffers)
- * is a fixed array in device memory that is created when the library is
- * loaded and held by every GPU that loads it until the process exits.  No
- * context is needed; the call runs on the current device.
- *   Arguments as topk_select, with n limited to 2^22 (4194304) keys; larger
- *   n returns TOPK_EINVAL and enqueues nothing.
+ * of the call (no counterpart in the paper).  Such callers include code
+ * running inside another framework's allocator or memory-pool callbacks
+ * (where allocating again would re-enter that allocator), latency-critical
+ * paths that cannot accept the device-wide synchronisation cudaMalloc /
+ * cudaFree may cause, and programs that fix their device memory at start-up.
+ * The library's scratch for this call (about 12 MiB: state, counters and two
+ * candidate buffers of 2^19 pairs) is a fixed array in device memory that is
+ * created when the library is loaded and held by every GPU that loads it
+ * until the process exits.  No context is needed; the call runs on the
+ * current device.
+ *   Arguments as topk_select (no params: the default tuning), with n limited
+ *   to 2^22 (4194304) keys; larger n returns TOPK_EINVAL and enqueues
+ *   nothing.  Every buffer (keys, outputs, d_status) must be memory of the
+ *   current device, else TOPK_EINVAL.
  *   d_status   NULL or one caller-owned uint32 in device memory: set to 0 by
  *              the call and to a topk_status code if the device work fails.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and sets kernel attributes; make that first call
- * before any stream capture.  The call itself calls no cudaMalloc, cudaFree
- * or other allocating routine.  All calls in the process share the one array
- * per device, which keeps the contents left by the last call: calls whose
- * work may overlap on the GPU (different streams, or threads) race and must
- * be serialised by the caller. */
+ *              With NULL, a failure of the device work is not reported to
+ *              the caller at all (the outputs are then undefined).
+ * The first call on a device does a one-time set-up there: it looks up the
+ * array's device address (cudaGetSymbolAddress) and sets the kernel
+ * attributes and launch geometry of all five key types.  Make that first
+ * call before any stream capture.  The call itself calls no cudaMalloc,
+ * cudaFree or other allocating routine.  All calls in the process share the
+ * one array per device, which keeps the contents left by the last call (each
+ * call clears what must start at zero): calls whose work may overlap on the
+ * GPU (different streams, or threads) race and must be serialised by the
+ * caller. */
 topk_status topk_select_noalloc(const void *d_keys, uint64_t n, uint64_t k,
                                 topk_dtype dtype, void *d_out_keys, uint32_t *d_out_idx,
                                 void *d_kth_key, uint32_t *d_kth_idx, uint32_t *d_status,

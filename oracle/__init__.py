@@ -59,6 +59,8 @@ class Oracle:
         lib.oracle_select_largest.restype = i32
         lib.oracle_pairs_before.argtypes = [vp, u64, i32, u64, i32, vp]
         lib.oracle_pairs_before.restype = i32
+        lib.oracle_check_selection.argtypes = [vp, u64, i32, u64, i32, vp, vp, u64, vp]
+        lib.oracle_check_selection.restype = i32
         lib.oracle_select_runs.argtypes = [vp, vp, u32, u64, vp, vp, vp]
         lib.oracle_select_runs.restype = i32
         lib.oracle_runs_delete_min.argtypes = [vp, vp, u32, vp, u64, vp, vp]
@@ -120,6 +122,26 @@ class Oracle:
                                         1 if descending else 0, _ptr(c)) != 0:
             raise ValueError("oracle_pairs_before rejected its arguments")
         return int(c[0])
+
+    def check_selection(self, keys: np.ndarray, dtype: str, k: int, sel_idx: np.ndarray, kth: int,
+                        out_keys: np.ndarray | None = None, kth_key: np.ndarray | None = None,
+                        descending: bool = False) -> int:
+        """0 if (sel_idx, out_keys, kth, kth_key) is exactly the k smallest
+        (largest) pairs with their input keys; else the code of the first
+        failed condition (see oracle.h)."""
+        a = _bits(keys, dtype)
+        sel = np.ascontiguousarray(sel_idx, dtype=np.uint32)
+        if sel.size != int(k):
+            return 2
+        ok = _ptr(_bits(out_keys, dtype)) if out_keys is not None else None
+        kk = _ptr(_bits(kth_key, dtype)) if kth_key is not None else None
+        keep = (out_keys, kth_key)  # alive during the call
+        r = self.lib.oracle_check_selection(_ptr(a), a.size, DTYPE_CODES[dtype], int(k),
+                                            1 if descending else 0, _ptr(sel), ok, int(kth), kk)
+        del keep
+        if r < 0:
+            raise ValueError("oracle_check_selection rejected its arguments")
+        return int(r)
 
     def select_runs(self, keys: np.ndarray, run_off: np.ndarray, k: int):
         """(split[p], kth_run, kth_pos) for multisequence selection of rank k."""
@@ -208,6 +230,45 @@ class Oracle:
                                           _ptr(kth)) != 0:
             raise ValueError("oracle_select_batched rejected its arguments")
         return sel[: int(out_off[-1])], out_off, kth[:rows]
+
+
+class CpuBaselines:
+    """The benchmark's timed CPU baselines (``cpu_baselines.cpp``): threaded
+    sort-and-take and one-core std::nth_element over float32 keys."""
+
+    def __init__(self, path: str):
+        lib = ctypes.CDLL(path)
+        u64, i32, vp = ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+        lib.cpu_sort_chunks_f32.argtypes = [vp, u64, i32, vp]
+        lib.cpu_sort_chunks_f32.restype = i32
+        lib.cpu_take_k.argtypes = [vp, u64, i32, u64, vp, vp]
+        lib.cpu_take_k.restype = i32
+        lib.cpu_nth_element_f32.argtypes = [vp, u64, u64, vp, vp]
+        lib.cpu_nth_element_f32.restype = i32
+        self.lib = lib
+
+    def sort_chunks(self, bits: np.ndarray, threads: int, work: np.ndarray):
+        b = np.ascontiguousarray(bits, dtype=np.uint32)
+        if self.lib.cpu_sort_chunks_f32(_ptr(b), b.size, int(threads), _ptr(work)) != 0:
+            raise ValueError("cpu_sort_chunks_f32 rejected its arguments")
+
+    def take_k(self, work: np.ndarray, threads: int, k: int, sel: np.ndarray) -> int:
+        kth = np.zeros(1, np.uint32)
+        if self.lib.cpu_take_k(_ptr(work), work.size, int(threads), int(k), _ptr(sel), _ptr(kth)) != 0:
+            raise ValueError("cpu_take_k rejected its arguments")
+        return int(kth[0])
+
+    def nth_element(self, bits: np.ndarray, k: int, work: np.ndarray) -> int:
+        b = np.ascontiguousarray(bits, dtype=np.uint32)
+        kth = np.zeros(1, np.uint32)
+        if self.lib.cpu_nth_element_f32(_ptr(b), b.size, int(k), _ptr(work), _ptr(kth)) != 0:
+            raise ValueError("cpu_nth_element_f32 rejected its arguments")
+        return int(kth[0])
+
+
+def cpu_baselines() -> CpuBaselines:
+    from .build import build_baselines
+    return CpuBaselines(build_baselines())
 
 
 _default = None

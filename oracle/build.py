@@ -28,7 +28,25 @@ def build(force: bool = False) -> str:
         for f in ("oracle.c", "oracle.h"))
     if force or not fresh:
         compile_source(SRC, LIB_PATH)
+    build_baselines(force)
     return LIB_PATH
+
+
+BASELINES_SRC = os.path.join(HERE, "cpu_baselines.cpp")
+BASELINES_LIB = os.path.join(HERE, "libcpu_baselines.so")
+
+
+def build_baselines(force: bool = False) -> str:
+    """The benchmark's timed CPU baselines (threaded sort-and-take, one-core
+    nth_element): g++, no host-specific flags."""
+    fresh = os.path.exists(BASELINES_LIB) and \
+        os.path.getmtime(BASELINES_LIB) >= os.path.getmtime(BASELINES_SRC)
+    if force or not fresh:
+        tmp = BASELINES_LIB + f".tmp{os.getpid()}"
+        subprocess.run(["g++", "-O2", "-std=c++17", "-Wall", "-fPIC", "-shared", "-pthread",
+                        BASELINES_SRC, "-o", tmp], check=True)
+        os.replace(tmp, BASELINES_LIB)
+    return BASELINES_LIB
 
 
 if __name__ == "__main__":

@@ -244,6 +244,60 @@ int oracle_pairs_before(const void *keys, uint64_t n, int dtype, uint64_t pos,
     return 0;
 }
 
+/* Whether a claimed answer is exactly the k smallest pairs (or, with
+ * descending = 1, the k largest), checked from the definition without a sort:
+ *   (1) the claimed rank-k pair (keys[kth], kth) has k - 1 pairs before it;
+ *   (2) the k claimed positions are distinct (a bitmap of n bits);
+ *   (3) no claimed pair comes after the rank-k pair;
+ *   (4) every claimed output key (out_keys, may be NULL) has the bits of the
+ *       input key at its position, and the claimed rank-k key (kth_key, may
+ *       be NULL) those of keys[kth].
+ * (1)-(3) leave exactly one set: k distinct pairs, none after the pair that
+ * has exactly k - 1 before it, are the k pairs up to it.  Returns 0 when all
+ * hold, the number of the first failed condition otherwise, -1 on bad
+ * arguments or allocation failure. */
+int oracle_check_selection(const void *keys, uint64_t n, int dtype, uint64_t k,
+                           int descending, const uint32_t *sel_idx, const void *out_keys,
+                           uint64_t kth, const void *kth_key)
+{
+    uint64_t before = 0, i, kv;
+    uint8_t *seen;
+    if (!keys || !sel_idx || !oracle_key_bytes(dtype) || k < 1 || k > n || kth >= n)
+        return -1;
+    if (oracle_pairs_before(keys, n, dtype, kth, descending, &before) != 0)
+        return -1;
+    if (before != k - 1)
+        return 1;
+    seen = (uint8_t *)calloc((size_t)(n / 8 + 1), 1);
+    if (!seen)
+        return -1;
+    kv = load_key(keys, kth, dtype);
+    for (i = 0; i < k; ++i) {
+        uint64_t x = sel_idx[i];
+        int d;
+        if (x >= n || (seen[x / 8] >> (x % 8)) & 1u) {
+            free(seen);
+            return 2;
+        }
+        seen[x / 8] |= (uint8_t)(1u << (x % 8));
+        d = oracle_key_cmp(dtype, load_key(keys, x, dtype), kv);
+        if (descending)
+            d = -d;
+        if (d > 0 || (d == 0 && x > kth)) {
+            free(seen);
+            return 3;
+        }
+        if (out_keys && load_key(out_keys, i, dtype) != load_key(keys, x, dtype)) {
+            free(seen);
+            return 4;
+        }
+    }
+    free(seen);
+    if (kth_key && load_key(kth_key, 0, dtype) != kv)
+        return 4;
+    return 0;
+}
+
 /* The run r with run_off[r] <= g < run_off[r+1] (bisection over the
  * non-decreasing offsets; empty runs are skipped because their interval is
  * empty). */

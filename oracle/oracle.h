@@ -70,6 +70,19 @@ int oracle_select(const void *keys, uint64_t n, int dtype, uint64_t k,
 int oracle_pairs_before(const void *keys, uint64_t n, int dtype, uint64_t pos,
                         int descending, uint64_t *count);
 
+/* Checks a claimed selection against the definition without sorting (for
+ * sizes where the full sort is slow): positions sel_idx[0..k) with output keys
+ * out_keys[0..k) (NULL: not checked), rank-k position kth and rank-k key
+ * kth_key[0] (NULL: not checked), for the k smallest (descending = 0) or the
+ * k largest (descending = 1).  Returns 0 if it is exactly that set with the
+ * right keys; 1 if the rank-k pair has the wrong rank, 2 if a position
+ * repeats or is out of range, 3 if a claimed pair comes after the rank-k
+ * pair, 4 if an output key differs from the input key at its position;
+ * -1 on bad arguments. */
+int oracle_check_selection(const void *keys, uint64_t n, int dtype, uint64_t k,
+                           int descending, const uint32_t *sel_idx, const void *out_keys,
+                           uint64_t kth, const void *kth_key);
+
 /* Multisequence selection over p runs stored back to back in `keys`
  * (u64 keys; run r is keys[run_off[r] .. run_off[r+1]) ).  Pairs are ordered
  * by (key, run, position), i.e. by (key, concatenated index).  split[r]

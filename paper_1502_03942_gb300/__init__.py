@@ -591,21 +591,24 @@ def topk_select_noalloc(keys, k: int, stream=None, out=None, status=None):
     """topk_select without any allocation inside the library (scratch in a
     fixed device array; n <= 2^22).  For callers that cannot allocate at the
     point of the call; ``out`` and ``status`` (one uint32 CUDA word) must then
-    be provided by the caller, otherwise they are allocated here.  Returns
-    the four outputs; the call does not wait."""
+    be provided by the caller, otherwise they are allocated here.  Runs on
+    ``keys``' device (on ``stream``, else that device's current stream).
+    Returns the four outputs; the call does not wait."""
     torch = _torch()
     if keys.dim() != 1 or not keys.is_cuda or not keys.is_contiguous():
         raise ValueError("keys must be a contiguous 1-D CUDA tensor")
-    if out is None:
-        kk = max(int(k), 1)
-        out = (torch.empty(kk, dtype=keys.dtype, device=keys.device),
-               torch.empty(kk, dtype=torch.uint32, device=keys.device),
-               torch.empty(1, dtype=keys.dtype, device=keys.device),
-               torch.empty(1, dtype=torch.uint32, device=keys.device))
-    ok, oi, kk_, ki = out
-    st = load_library().topk_select_noalloc(
-        _ptr(keys), keys.numel(), int(k), dtype_code(keys), _ptr(ok), _ptr(oi), _ptr(kk_), _ptr(ki),
-        _ptr(status) if status is not None else None, _stream_ptr(stream))
+    with torch.cuda.device(keys.device):
+        if out is None:
+            kk = max(int(k), 1)
+            out = (torch.empty(kk, dtype=keys.dtype, device=keys.device),
+                   torch.empty(kk, dtype=torch.uint32, device=keys.device),
+                   torch.empty(1, dtype=keys.dtype, device=keys.device),
+                   torch.empty(1, dtype=torch.uint32, device=keys.device))
+        ok, oi, kk_, ki = out
+        st = load_library().topk_select_noalloc(
+            _ptr(keys), keys.numel(), int(k), dtype_code(keys), _ptr(ok), _ptr(oi), _ptr(kk_), _ptr(ki),
+            _ptr(status) if status is not None else None,
+            _stream_ptr(stream if stream is not None else torch.cuda.current_stream(keys.device)))
     _check(st, "topk_select_noalloc")
     return out
 

@@ -95,6 +95,9 @@ inline cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, siz
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Counters of the last sorted-runs call on the context (rounds).
+topk_status runs_last_stats(topk_ctx* ctx, topk_stats* out);
+
 // Batched selection with rows given by device pointer arrays (serving).
 topk_status batched_by_pointers(topk_ctx* ctx, topk_dtype dtype, uint32_t rows, const void* ptrs,
                                 cudaStream_t st);

@@ -599,6 +599,14 @@ static u32 runs_rounds_for(u64 p, u64 k, u32 d) {
     return r;
 }
 
+topk_status runs_last_stats(topk_ctx* ctx, topk_stats* out) {
+    RunsState s;
+    if (cudaMemcpy(&s, ctx->d_state, sizeof(RunsState), cudaMemcpyDeviceToHost) != cudaSuccess) return TOPK_ECUDA;
+    out->levels_grid = s.rounds_grid;
+    out->levels_block = s.rounds_block;
+    return TOPK_OK;
+}
+
 } // namespace topk
 
 using namespace topk;

@@ -1113,7 +1113,13 @@ static topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, voi
 // address is looked up once per device with cudaGetSymbolAddress.
 
 constexpr u64 NOALLOC_MAX_N = 1ull << 22;  // largest n accepted (4 Mi keys)
-constexpr u64 NOALLOC_CAP = 1ull << 18;    // candidate pairs per buffer
+// Candidate pairs per buffer.  The context path sizes its buffers as
+// candidate_capacity(n, k): twice the expected first bracket plus 4 T, which
+// is largest at k = n/2 and, for n = 2^22 with the default tuning, is about
+// 3.4e5 pairs for 32-bit keys (s = 16384) and 4.2e5 for 64-bit keys
+// (s = 8192).  2^19 covers both, so no accepted call overflows more often
+// than the same call through a context; the set-up checks this relation.
+constexpr u64 NOALLOC_CAP = 1ull << 19;
 constexpr size_t NA_OFF_STATE = 0;         // SelState
 constexpr size_t NA_OFF_WORDS = 4096;      // [0] error, [1] reduction done, [2] pass done, [3] sample count
 constexpr size_t NA_OFF_HIST = 8192;       // HIST_BINS u32
@@ -1122,18 +1128,40 @@ constexpr size_t NA_PART_BYTES = 64 * 1024;
 constexpr size_t NA_OFF_SAMP = NA_OFF_PART + NA_PART_BYTES; // sample, Lim<32>::ELEMS * 8 = Lim<64>::ELEMS * 16 bytes
 constexpr size_t NA_SAMP_BYTES = 128 * 1024;
 constexpr size_t NA_OFF_CAND = NA_OFF_SAMP + NA_SAMP_BYTES;
-constexpr size_t NA_BYTES = NA_OFF_CAND + 2 * NOALLOC_CAP * (8 + 4); // about 6.2 MiB
+constexpr size_t NA_BYTES = NA_OFF_CAND + 2 * NOALLOC_CAP * (8 + 4); // about 12.2 MiB
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[64] = {};
 
+// Kernel attributes and the launch-geometry queries of every key type, so
+// that no later call on this device makes them (they are made once per
+// process and key type otherwise, on the first call with 1 < k < n).
+template <int DT> static topk_status noalloc_prepare_dt(int sms) {
+    topk_status rs = set_smem_attrs<DT>();
+    if (rs != TOPK_OK) return rs;
+    (void)tma_grid<DT, false>(sms);
+    (void)tma_grid<DT, true>(sms);
+    (void)pass_grid<DT>(sms, true);
+    return cudaGetLastError() == cudaSuccess ? TOPK_OK : TOPK_ECUDA;
+}
+
 // Device address of the array on the current device `dev` (set-up on first use).
-static topk_status noalloc_base(int dev, char** out) {
+static topk_status noalloc_base(int dev, int sms, char** out) {
     if (dev < 0 || dev >= 64) return TOPK_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
+        // the buffers must hold what the context path would allocate at the size limit
+        if (candidate_capacity(NOALLOC_MAX_N, NOALLOC_MAX_N / 2, make_tuning<32>(nullptr, sms)) > NOALLOC_CAP ||
+            candidate_capacity(NOALLOC_MAX_N, NOALLOC_MAX_N / 2, make_tuning<64>(nullptr, sms)) > NOALLOC_CAP)
+            return TOPK_EINTERNAL;
+        topk_status rs = noalloc_prepare_dt<DT_U32>(sms);
+        if (rs == TOPK_OK) rs = noalloc_prepare_dt<DT_I32>(sms);
+        if (rs == TOPK_OK) rs = noalloc_prepare_dt<DT_F32>(sms);
+        if (rs == TOPK_OK) rs = noalloc_prepare_dt<DT_BF16>(sms);
+        if (rs == TOPK_OK) rs = noalloc_prepare_dt<DT_U64>(sms);
+        if (rs != TOPK_OK) return rs;
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
@@ -1143,6 +1171,16 @@ static topk_status noalloc_base(int dev, char** out) {
     }
     *out = static_cast<char*>(g_noalloc_addr[dev]);
     return TOPK_OK;
+}
+
+// Whether `p` is device (or managed) memory of device `dev`.
+static bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 template <int DT>
@@ -1255,9 +1293,13 @@ topk_status topk_select_noalloc(const void* d_keys, uint64_t n, uint64_t k, topk
     if (reinterpret_cast<uintptr_t>(d_out_keys) % (uintptr_t)w) return TOPK_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TOPK_ECUDA;
+    // every buffer must live on the current device, whose array and stream the call uses
+    if (!on_device(d_keys, dev) || !on_device(d_out_keys, dev) || !on_device(d_out_idx, dev) ||
+        !on_device(d_kth_key, dev) || !on_device(d_kth_idx, dev) || (d_status && !on_device(d_status, dev)))
+        return TOPK_EINVAL;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return TOPK_ECUDA;
     char* base = nullptr;
-    topk_status rs = noalloc_base(dev, &base);
+    topk_status rs = noalloc_base(dev, sms, &base);
     if (rs != TOPK_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     switch (dtype) {
@@ -1289,6 +1331,7 @@ topk_status topk_ctx_reserve(topk_ctx* ctx, uint64_t n, topk_dtype dtype) {
 topk_status topk_last_stats(topk_ctx* ctx, topk_stats* out) {
     if (!ctx || !out) return TOPK_EINVAL;
     *out = topk_stats{};
+    if (ctx->last_kind == LAST_RUNS) return runs_last_stats(ctx, out);
     if (ctx->last_kind != LAST_SELECT) return TOPK_OK;
     SelState s;
     if (cudaMemcpy(&s, ctx->d_state, sizeof(SelState), cudaMemcpyDeviceToHost) != cudaSuccess) return TOPK_ECUDA;

@@ -517,8 +517,51 @@ def check_pairs_before(orc, seed=9):
     return fails
 
 
+def check_selection_checker(orc, seed=10):
+    """The sort-free checker accepts the brute-force answer (Python's own
+    value order) in both directions and rejects answers with one planted
+    error each: an unselected position swapped in, a repeated position, the
+    rank-k position moved by one, an output key not the input key."""
+    fails = []
+    g = np.random.Generator(np.random.Philox(seed))
+    for dtype in ("u32", "i32", "f32", "bf16", "u64"):
+        for n in (2, 9, 40):
+            keys = random_bits(g, dtype, n)
+            vk = VALUE_KEY[dtype]
+            for desc in (False, True):
+                f = (lambda v: _neg(v)) if desc else (lambda v: v)
+                order = sorted(range(n), key=lambda i: (f(vk(int(keys[i]))), i))
+                for k in (1, n // 2, n - 1):
+                    if k < 1:
+                        continue
+                    sel = np.array(order[:k], np.uint32)
+                    kth = order[k - 1]
+                    good = orc.check_selection(keys, dtype, k, sel, kth, keys[sel], keys[kth:kth + 1],
+                                               descending=desc)
+                    if good != 0:
+                        fails.append(f"checker rejects the answer {dtype} n={n} k={k} desc={desc}: {good}")
+                        continue
+                    bad = sel.copy()
+                    if k >= 2:
+                        bad[0] = order[k]  # an unselected pair in place of a selected one
+                        if orc.check_selection(keys, dtype, k, bad, kth, descending=desc) == 0:
+                            fails.append(f"checker takes a swapped-in position {dtype} n={n} k={k}")
+                        bad = sel.copy()
+                        bad[1] = bad[0]
+                        if orc.check_selection(keys, dtype, k, bad, kth, descending=desc) != 2:
+                            fails.append(f"checker takes a repeated position {dtype} n={n} k={k}")
+                    if orc.check_selection(keys, dtype, k, sel, order[k], descending=desc) != 1:
+                        fails.append(f"checker takes the rank-(k+1) pair as rank k {dtype} n={n} k={k}")
+                    wrong = keys[sel].copy()
+                    wrong[-1] ^= 1
+                    if orc.check_selection(keys, dtype, k, sel, kth, wrong, descending=desc) != 4:
+                        fails.append(f"checker takes a wrong output key {dtype} n={n} k={k}")
+    return fails
+
+
 ALL_CHECKS = [check_brute_force, check_exhaustive_ties, check_library_special_cases,
               check_total_order_fixture, check_bf16_exhaustive, check_runs_vs_merge,
               check_batched_rows, check_delete_min_vs_heap, check_philox_kat,
               check_pac_worked_example, check_frequent_vs_counter, check_bernoulli_decisions,
-              check_frequent_plan, check_largest_brute_force, check_pairs_before]
+              check_frequent_plan, check_largest_brute_force, check_pairs_before,
+              check_selection_checker]

@@ -43,6 +43,8 @@ MUTATIONS = {
     "pac_first_term_2n": ("double a = 3.0 / k * log(4.0 * n / delta);",
                           "double a = 3.0 / k * log(2.0 * n / delta);"),
     "pairs_before_ties_inclusive": ("if (d < 0 || (d == 0 && i < pos))", "if (d < 0 || (d == 0 && i <= pos))"),
+    "checker_rank_loose": ("if (before != k - 1)\n        return 1;", "if (before > k)\n        return 1;"),
+    "checker_no_bound": ("if (d > 0 || (d == 0 && x > kth)) {", "if (d > 0) {"),
     "take_k_minus_one": ("for (i = 0; i < k; ++i)             /* ranks 1..k */",
                          "for (i = 1; i < k; ++i)             /* ranks 1..k */"),
 }

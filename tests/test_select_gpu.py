@@ -238,22 +238,3 @@ def test_largest_heavy_ties_and_specials(tk, ctx, orc, name):
     p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
     for k in ks_for(200003):
         check_largest(keys, name, k, tk.topk_select(ctx, d, k, params=p), orc)
-
-
-def test_largest_full_size_properties(tk, ctx, orc):
-    """n = 2^28 f32 N(0,1) keys, the 1024 and the n/2 largest: every selected
-    key is at or above the rank-k key, the rest at or below it, ties split by
-    position, the count of keys above it below k (checked with torch)."""
-    import torch
-    n = 1 << 28
-    d = wl.device_f32_dataset("normal", n, seed=31)
-    p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
-    for k in (1024, n // 2):
-        ok, oi, kk, ki = tk.topk_select(ctx, d, k, params=p)
-        kth = kk.view(torch.float32)[0]
-        assert torch.all(d[oi.view(torch.int32).long()] >= kth)
-        above = int((d > kth).sum().item())
-        equal_before = int(((d == kth) & (torch.arange(n, device=d.device) <= ki.view(torch.int32)[0].long())).sum().item())
-        assert above + equal_before == k
-        assert int(torch.unique(oi.view(torch.int32)).numel()) == k
-

@@ -605,15 +605,21 @@ template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) 
 // bits.  The 16 slots go in chunks of CH slots, at most CH * 32 <= QCAP hits
 // each, in turn, so one flush always makes room; the chunks share one copy
 // of the code.  pos(q) must accept a lane-dependent q.
-template <int DT, class CT, class KeyT, class PosF>
+template <int DT, bool KEY_ONLY = false, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
                                                 const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
-    classify_sparse<DT>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q, qs);
+    classify_sparse<DT, KEY_ONLY>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q,
+                                  qs);
 }
 
 // The same, with key_at(q) giving slot q's key for a lane-dependent q (for
 // instance from a shared-memory stage instead of a tree of selects).
-template <int DT, class CT, class KeyT, class PosF, class KeyAt>
+//
+// KEY_ONLY (a window starting at the smallest pair, lo = 0): an element is
+// queued when its key is at most the upper pivot's key, one comparison of
+// the key alone; the few queued elements equal to that key but beyond the
+// pivot's position are dropped when the queue is classified on the pair.
+template <int DT, bool KEY_ONLY = false, class CT, class KeyT, class PosF, class KeyAt>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, KeyAt key_at, u32 valid, CT lo,
                                                 CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
                                                 QState& qs) {
@@ -625,8 +631,14 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
     static_assert(CH * 32 <= QCAP, "queue too small for a chunk");
     static_assert(CH * 32 < (1u << FB), "chunk count does not fit its field");
     u32 hit = 0;
+    if (KEY_ONLY) {
+        const KeyT prk = (KeyT)C::key(pr);
 #pragma unroll
-    for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
+        for (int s = 0; s < 16; ++s) hit |= (u32)(kk[s] <= prk) << s;
+    } else {
+#pragma unroll
+        for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
+    }
     hit &= valid;
     if (!__any_sync(0xffffffffu, hit)) return;
     u32 cnt = 0;

@@ -317,6 +317,169 @@ template <int DT> struct Sink {
     }
 };
 
+// ---------------------------------------------- bounds on raw key bits
+// Whether image(x) <= T (or >= T) for the order-preserving image of a key
+// type, decided by one integer comparison of the raw bits x against a bound
+// derived from T once, instead of transforming every key.  For the IEEE
+// types the image of a non-negative pattern is x + 2^(w-1) and that of a
+// negative one ~x (w = 32 for f32, 16 for bf16), so
+//   image(x) <= T, T >= 2^(w-1):  x <= T - 2^(w-1)  (x as a signed w-bit integer)
+//   image(x) <= T, T <  2^(w-1):  x >= ~T           (unsigned)
+//   image(x) >= T, T >= 2^(w-1):  x >= T - 2^(w-1)  (signed)
+//   image(x) >= T, T <  2^(w-1):  x <= ~T           (unsigned)
+// i32's image is x ^ 2^31, a signed comparison; u32 and u64 are their own
+// images.  The descending codes (image = ascending image ^ FLIP) turn
+// image <= T into ascending image >= T ^ FLIP.
+enum : u32 { RB_LE_S = 0, RB_LE_U = 1, RB_GE_S = 2, RB_GE_U = 3 };
+
+template <int DT> struct RawBound {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    typedef key_t cmp_t; // u32 for 32- and 16-bit keys, u64 for u64
+    static constexpr int B = DT % DT_DESC;
+    u32 mode;
+    cmp_t v;
+
+    __device__ static RawBound make(u32 m, cmp_t v) { RawBound r; r.mode = m; r.v = v; return r; }
+    __device__ static RawBound asc_le(key_t T) {
+        if (B == DT_U32 || B == DT_U64) return make(RB_LE_U, T);
+        if (B == DT_I32) return make(RB_LE_S, (cmp_t)(T ^ 0x80000000u));
+        constexpr key_t H = B == DT_BF16 ? 0x8000u : 0x80000000u;
+        constexpr key_t M = B == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu;
+        return T >= H ? make(RB_LE_S, (cmp_t)(T - H)) : make(RB_GE_U, (cmp_t)(~T & M));
+    }
+    __device__ static RawBound asc_ge(key_t T) {
+        if (B == DT_U32 || B == DT_U64) return make(RB_GE_U, T);
+        if (B == DT_I32) return make(RB_GE_S, (cmp_t)(T ^ 0x80000000u));
+        constexpr key_t H = B == DT_BF16 ? 0x8000u : 0x80000000u;
+        constexpr key_t M = B == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu;
+        return T >= H ? make(RB_GE_S, (cmp_t)(T - H)) : make(RB_LE_U, (cmp_t)(~T & M));
+    }
+    // the bound for image(x) <= T
+    __device__ static RawBound le(key_t T) {
+        if constexpr (DT >= DT_DESC) return asc_ge((key_t)(T ^ K::FLIP));
+        else return asc_le(T);
+    }
+    // signed value of a raw pattern (sign-extended from its own width)
+    __device__ static int sval(raw_t x) {
+        if constexpr (sizeof(raw_t) == 2) return (int)(int16_t)x;
+        else return (int)(u32)x;
+    }
+    template <u32 MODE> __device__ static bool test(raw_t x, cmp_t v) {
+        if constexpr (sizeof(raw_t) == 8) {
+            return MODE == RB_LE_U ? (u64)x <= (u64)v : (u64)x >= (u64)v;
+        } else {
+            if constexpr (MODE == RB_LE_S) return sval(x) <= (int)(u32)v;
+            else if constexpr (MODE == RB_LE_U) return (u32)x <= (u32)v;
+            else if constexpr (MODE == RB_GE_S) return sval(x) >= (int)(u32)v;
+            else return (u32)x >= (u32)v;
+        }
+    }
+};
+
+// Masks of a tile's 16 slots whose pair is below pl (ma) and at most pr (le),
+// for a tile whose positions all lie on one side of each pivot's position:
+// ties with a pivot's key are then decided for the whole tile, and each
+// slot costs two comparisons of raw bits.  `any_a` / `any_l` false: no slot
+// qualifies.
+template <int DT, u32 MA, u32 MB>
+__device__ __forceinline__ void tile_masks_raw(const typename Key<DT>::raw_t (&rr)[16], typename RawBound<DT>::cmp_t va,
+                                               typename RawBound<DT>::cmp_t vb, bool any_a, bool any_l, u32& ma,
+                                               u32& le) {
+    typedef RawBound<DT> R;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        ma |= (u32)(any_a && R::template test<MA>(rr[q], va)) << q;
+        le |= (u32)(any_l && R::template test<MB>(rr[q], vb)) << q;
+    }
+}
+
+// The bounds of the tiles that contain neither pivot's position, computed
+// once per pass: pair < pl  <=>  image <= a_le and pair <= pr  <=>
+// image <= b_le, where a tile wholly before the pivot's position takes the
+// pivot's key itself as the bound and one wholly after it the next smaller
+// key (no element qualifies when there is none).
+template <int DT> struct TileBounds {
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename Key<DT>::key_t key_t;
+    RawBound<DT> ba_before, ba_after, bb_before, bb_after;
+    bool any_a_after, any_l_after;
+    u32 plx, prx;
+    __device__ static TileBounds make(typename C::t pl, typename C::t pr) {
+        TileBounds t;
+        const key_t plk = (key_t)C::key(pl), prk = (key_t)C::key(pr);
+        t.plx = C::idx(pl);
+        t.prx = C::idx(pr);
+        t.ba_before = RawBound<DT>::le(plk);
+        t.bb_before = RawBound<DT>::le(prk);
+        t.ba_after = RawBound<DT>::le((key_t)(plk - 1));
+        t.bb_after = RawBound<DT>::le((key_t)(prk - 1));
+        t.any_a_after = plk != 0;
+        t.any_l_after = prk != 0;
+        return t;
+    }
+    // The bounds of tile [tb, te]; false when it contains a pivot's position
+    // (then compare pairs).
+    __device__ __forceinline__ bool get(u32 tb, u32 te, RawBound<DT>& ba, RawBound<DT>& bb, bool& any_a,
+                                        bool& any_l) const {
+        if ((plx >= tb && plx <= te) || (prx >= tb && prx <= te)) return false;
+        const bool sa = te < plx;  // wholly before pl's position: ties with pl's key are in a
+        const bool sl = te <= prx; // wholly at or before pr's position: ties with pr's key are <= pr
+        ba.mode = sa ? ba_before.mode : ba_after.mode;
+        ba.v = sa ? ba_before.v : ba_after.v;
+        bb.mode = sl ? bb_before.mode : bb_after.mode;
+        bb.v = sl ? bb_before.v : bb_after.v;
+        any_a = sa || any_a_after;
+        any_l = sl || any_l_after;
+        return true;
+    }
+};
+
+// The two comparison kinds RawBound<DT>::le can produce: M0 for a bound in
+// the non-negative half of an IEEE type (and the only kind of the integer
+// types), M1 for a bound in the negative half.
+template <int DT> struct RawModes {
+    static constexpr int B = DT % DT_DESC;
+    static constexpr bool DESC = DT >= DT_DESC;
+    static constexpr bool IEEE = B == DT_F32 || B == DT_BF16;
+    static constexpr u32 M0 = (B == DT_U32 || B == DT_U64) ? (DESC ? RB_GE_U : RB_LE_U) : (DESC ? RB_GE_S : RB_LE_S);
+    static constexpr u32 M1 = IEEE ? (DESC ? RB_LE_U : RB_GE_U) : M0;
+};
+
+// The mask of a tile's slots whose pair is at most pr, from the raw bits.
+template <int DT, u32 MB>
+__device__ __forceinline__ u32 tile_le_raw(const typename Key<DT>::raw_t (&rr)[16], typename RawBound<DT>::cmp_t vb) {
+    u32 le = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) le |= (u32)RawBound<DT>::template test<MB>(rr[q], vb) << q;
+    return le;
+}
+template <int DT>
+__device__ __forceinline__ u32 tile_le_dispatch(const typename Key<DT>::raw_t (&rr)[16], const RawBound<DT>& bb,
+                                                bool any_l) {
+    typedef RawModes<DT> M;
+    if (!any_l) return 0;
+    if (!M::IEEE || bb.mode == M::M0) return tile_le_raw<DT, M::M0>(rr, bb.v);
+    return tile_le_raw<DT, M::M1>(rr, bb.v);
+}
+
+// tile_masks_raw with the comparison kinds of (ba, bb), chosen at run time
+// among the combinations the key type can produce.
+template <int DT>
+__device__ __forceinline__ void tile_masks_dispatch(const typename Key<DT>::raw_t (&rr)[16], const RawBound<DT>& ba,
+                                                    const RawBound<DT>& bb, bool any_a, bool any_l, u32& ma, u32& le) {
+    typedef RawModes<DT> M;
+    if constexpr (!M::IEEE) {
+        tile_masks_raw<DT, M::M0, M::M0>(rr, ba.v, bb.v, any_a, any_l, ma, le);
+    } else {
+        if (ba.mode == M::M0 && bb.mode == M::M0) tile_masks_raw<DT, M::M0, M::M0>(rr, ba.v, bb.v, any_a, any_l, ma, le);
+        else if (ba.mode == M::M1 && bb.mode == M::M1) tile_masks_raw<DT, M::M1, M::M1>(rr, ba.v, bb.v, any_a, any_l, ma, le);
+        else if (ba.mode == M::M1) tile_masks_raw<DT, M::M1, M::M0>(rr, ba.v, bb.v, any_a, any_l, ma, le);
+        else tile_masks_raw<DT, M::M0, M::M1>(rr, ba.v, bb.v, any_a, any_l, ma, le);
+    }
+}
+
 // ------------------------------------------------------------ the pass
 // Streams the source in tiles of NT*16 elements, classifies every element
 // against (lo, pl, pr) and compacts a and b.  A tile with neither costs one
@@ -605,41 +768,24 @@ template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) 
 // bits.  The 16 slots go in chunks of CH slots, at most CH * 32 <= QCAP hits
 // each, in turn, so one flush always makes room; the chunks share one copy
 // of the code.  pos(q) must accept a lane-dependent q.
-template <int DT, bool KEY_ONLY = false, class CT, class KeyT, class PosF>
+template <int DT, class CT, class KeyT, class PosF>
 __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
                                                 const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
-    classify_sparse<DT, KEY_ONLY>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q,
-                                  qs);
+    classify_sparse<DT>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q, qs);
 }
 
-// The same, with key_at(q) giving slot q's key for a lane-dependent q (for
-// instance from a shared-memory stage instead of a tree of selects).
-//
-// KEY_ONLY (a window starting at the smallest pair, lo = 0): an element is
-// queued when its key is at most the upper pivot's key, one comparison of
-// the key alone; the few queued elements equal to that key but beyond the
-// pivot's position are dropped when the queue is classified on the pair.
-template <int DT, bool KEY_ONLY = false, class CT, class KeyT, class PosF, class KeyAt>
-__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, KeyAt key_at, u32 valid, CT lo,
-                                                CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
-                                                QState& qs) {
-    typedef Comp<Key<DT>::KW> C;
+// The appending step alone, for a hit mask computed by the caller (bit q:
+// slot q's pair is at most pr); key_at(q) gives slot q's key image for a
+// lane-dependent q.
+template <int DT, class CT, class PosF, class KeyAt>
+__device__ __forceinline__ void sparse_append_hits(u32 hit, PosF pos, KeyAt key_at, CT lo, CT pl, CT pr,
+                                                   const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
     constexpr u32 QCAP = (u32)WarpQ<Key<DT>::KW>::QCAP;
     constexpr u32 CH = QCAP >= 8 * 32 ? 8 : 4;    // slots per chunk
     constexpr u32 NCH = 16 / CH;                  // chunks per tile
     constexpr u32 FB = 32 / NCH;                  // bits per packed chunk count
     static_assert(CH * 32 <= QCAP, "queue too small for a chunk");
     static_assert(CH * 32 < (1u << FB), "chunk count does not fit its field");
-    u32 hit = 0;
-    if (KEY_ONLY) {
-        const KeyT prk = (KeyT)C::key(pr);
-#pragma unroll
-        for (int s = 0; s < 16; ++s) hit |= (u32)(kk[s] <= prk) << s;
-    } else {
-#pragma unroll
-        for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
-    }
-    hit &= valid;
     if (!__any_sync(0xffffffffu, hit)) return;
     u32 cnt = 0;
 #pragma unroll
@@ -669,6 +815,19 @@ __device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, 
         }
         qs.nq += th;
     }
+}
+
+// The same, with key_at(q) giving slot q's key for a lane-dependent q (for
+// instance from a shared-memory stage instead of a tree of selects).
+template <int DT, class CT, class KeyT, class PosF, class KeyAt>
+__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, KeyAt key_at, u32 valid, CT lo,
+                                                CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
+                                                QState& qs) {
+    typedef Comp<Key<DT>::KW> C;
+    u32 hit = 0;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
+    sparse_append_hits<DT>(hit & valid, pos, key_at, lo, pl, pr, sink, q, qs);
 }
 
 // Register path in sparse mode.

@@ -176,7 +176,7 @@ template <int KW> struct PivotSmem {
     ct wres[2];
 };
 
-constexpr u32 WARP_SELECT_MAX = 4096; // bins up to this size are ranked by one warp
+constexpr u32 WARP_SELECT_MAX = 512; // bins up to this size are ranked by one warp, larger ones by the block
 
 template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, int first) {
     grid_dep_wait();
@@ -464,21 +464,37 @@ template <int DT, bool DENSE = false> struct TmaCfg {
     static constexpr int MIN_BLOCKS = DENSE ? (W == 8 ? 2 : 3) : 1;
 };
 
-// MODE: 0 sparse (warp queues), 1 dense, 2 dense with a narrowed window.
-template <int DT, int MODE>
-__device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
-                            uint64_t* empty, u64 my_n, u32* dead, PassSmem<TMA_CONS>& ps, WarpQ<Key<DT>::KW>& wq) {
+// Raw key bits of this thread's 16 slots from a stage (slot q at vector
+// q / EPV of the thread, element q % EPV).
+template <int DT>
+__device__ __forceinline__ void load_raw_stage(const unsigned char* stage, typename Key<DT>::raw_t (&rr)[16]) {
+    uint4 v[InputSrc<DT>::NV];
+    const uint4* sp = reinterpret_cast<const uint4*>(stage);
+#pragma unroll
+    for (int j = 0; j < InputSrc<DT>::NV; ++j) v[j] = sp[j * TMA_CONS + threadIdx.x];
+    InputSrc<DT>::unpack_raw(v, rr);
+}
+
+// Sparse first level (few elements in a and b): the elements whose pair is
+// at most pr are appended to the warp's queue (select_core.cuh); a tile that
+// contains neither pivot's position finds them with one comparison of raw
+// key bits per element (tile_bounds), the rare other tile on the pair.
+template <int DT>
+__device__ void tma_consume_sparse(const SelArgs& a, const SelState& s, const unsigned char* stages, uint64_t* full,
+                                   uint64_t* empty, u64 my_n, u32* dead, WarpQ<Key<DT>::KW>& wq) {
     typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
     typedef Comp<K::KW> C;
     typedef typename C::t ct;
     typedef TmaCfg<DT> Cfg;
-    typedef SyncNamed<1, TMA_CONS> Sync;
+    constexpr u32 EPV = InputSrc<DT>::EPV;
     const Sink<DT> sink = make_sink<DT>(a, s);
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
     const u32 lane = lane_id();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0: input is 16-byte aligned
     QState qs = QState::make();
+    const TileBounds<DT> tbd = TileBounds<DT>::make(pl, pr);
     for (u64 i = 0; i < my_n; ++i) {
         const u32 stg = (u32)(i % Cfg::STAGES);
         const u32 parity = (u32)((i / Cfg::STAGES) & 1);
@@ -489,24 +505,30 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
             if (lane == 0) latch(a.err, ST_ETIMEOUT);
         }
         ok = __all_sync(0xffffffffu, ok);
-        key_t kk[16];
-        const unsigned char* sb = stages + (size_t)stg * Cfg::BYTES;
-        if (ok) {
-            InputSrc<DT>::template load16_smem<TMA_CONS>(reinterpret_cast<const uint4*>(sb), kk);
-        } else {
-#pragma unroll
-            for (int q = 0; q < 16; ++q) kk[q] = 0;
-        }
         // positions in 32 bits (inputs hold fewer than 2^32 keys): slot q of
         // this thread is ib + (q / EPV) * TMA_CONS * EPV + q % EPV
-        constexpr u32 EPV = InputSrc<DT>::EPV;
-        const u32 ib = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE) + threadIdx.x * EPV;
+        const u32 tb = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE);
+        const u32 ib = tb + threadIdx.x * EPV;
         auto pos = [&](int q) -> u32 { return ib + (u32)(q / (int)EPV) * (TMA_CONS * EPV) + (u32)(q % (int)EPV); };
-        const u32 valid = ok ? 0xFFFFu : 0u;
+        raw_t rr[16];
+        u32 hit = 0;
+        if (ok) {
+            load_raw_stage<DT>(stages + (size_t)stg * Cfg::BYTES, rr);
+            RawBound<DT> ba, bb;
+            bool any_a, any_l;
+            if (tbd.get(tb, tb + Cfg::TILE - 1, ba, bb, any_a, any_l)) {
+                hit = tile_le_dispatch<DT>(rr, bb, any_l);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) hit |= (u32)(C::make(K::fwd(rr[q]), pos(q)) <= pr) << q;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 16; ++q) rr[q] = 0;
+        }
         __syncwarp();
         if (ok && lane == 0) mbar_arrive(&empty[stg]); // keys are in registers: the stage may be refilled
-        if (MODE == 0) classify_sparse<DT, true>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
-        else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
+        sparse_append_hits<DT>(hit, pos, [&](u32 sq) { return K::fwd(pick16(rr, sq)); }, lo, pl, pr, sink, wq, qs);
     }
     // the ragged last tile, read directly by the block that owns it
     const u64 nfull = s.m_src / Cfg::TILE;
@@ -516,30 +538,27 @@ __device__ void tma_consume(const SelArgs& a, const SelState& s, const unsigned 
         const u64 tb = nfull * (u64)Cfg::TILE;
         const u32 valid = isrc.template load16<TMA_CONS>(tb, kk, ii);
         auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
-        if (MODE == 0) classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
-        else classify_emit<TMA_CONS, true, MODE == 2, Sync>(kk, pos, valid, lo, pl, pr, sink, ps);
+        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
     }
-    if (MODE == 0) queue_drain<DT>(wq, qs, sink, lo, pl, pr);
+    queue_drain<DT>(wq, qs, sink, lo, pl, pr);
 }
 
 // Dense first level (many elements in a; the window starts at the smallest
 // pair).  Output room is reserved per tile with one atomic per class, but
-// the reservation of tile i is issued before the elements of tile i-1 are
-// written, so its latency overlaps real work; tile i-1 is re-read from its
-// shared-memory stage, held until then.  Two threads take turns issuing the
-// atomics so that neither waits on its own pending result.
+// the reservation of tile i is issued right after the block's one barrier
+// of iteration i and published before the barrier of iteration i+1, so its
+// latency overlaps the work of a whole tile; tile i-1 is written after that
+// barrier, re-read from its shared-memory stage, which is held until then.
+// Two threads take turns issuing the atomics.
 //
-// Classification works on the key images alone: a key below the lower
-// pivot's key is in a, a key above the upper pivot's key in c; only keys
-// from the one to the other (the candidates b and the ties with a pivot's
-// key, a few per cent of a tile) are compared on the whole (key, position)
-// pair, one lane at a time over its own such slots.  Per slot a warp ballot
-// holds which lanes' elements are in a; the ballots of tile i-1 are kept in
-// registers, so at emission each lane finds its rank among the warp's
-// selected elements of the slot with one population count, and one store
+// A tile that contains neither pivot's position is classified with two
+// comparisons of raw key bits per element (tile_bounds): ties with a pivot's
+// key are decided for the whole tile by which side of the pivot's position
+// it lies on.  a-elements leave by per-slot warp ballots: one store
 // instruction per slot writes the warp's selected keys (and one their
-// positions) to consecutive addresses.  b-elements are few; each lane
-// writes its own at an offset from one warp scan.
+// positions) to consecutive addresses, the run pointers advancing by the
+// slot's count.  b-elements are few; each lane writes its own at an offset
+// from one warp scan.
 struct DenseSmem {
     u32 wa[2][TMA_CONS / 32], wb[2][TMA_CONS / 32]; // per-warp counts, by tile parity
     u64 oa[2][TMA_CONS / 32], ob[2][TMA_CONS / 32]; // per-warp offsets inside the tile
@@ -557,29 +576,21 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
     typedef TmaCfg<DT, true> Cfg;
     typedef SyncNamed<1, TMA_CONS> Sync;
     constexpr int EPV = InputSrc<DT>::EPV;
-    constexpr int NV = InputSrc<DT>::NV;
     constexpr u32 STRIDE = TMA_CONS * EPV; // index distance between a thread's vectors
     const Sink<DT> sink = make_sink<DT>(a, s);
     const ct pl = C::from128(s.pl), pr = C::from128(s.pr);
-    const key_t plk = (key_t)C::key(pl), span = (key_t)((key_t)C::key(pr) - plk);
     const u32 warp = threadIdx.x >> 5, lane = lane_id(), below = lanemask_lt();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0
-    // slot q of this thread in a stage: byte offset from the thread's first vector
-    auto slot_off = [](u32 q) -> u32 { return (q / EPV) * (TMA_CONS * 16u) + (q % EPV) * (u32)sizeof(raw_t); };
-    u32 bal_prev[16]; // per slot: the lanes whose element of tile i-1 is in a
-#pragma unroll
-    for (int q = 0; q < 16; ++q) bal_prev[q] = 0;
-    u32 mb_prev = 0, stg_prev = 0, ib_prev = 0;
+    const key_t plk = (key_t)C::key(pl), prk = (key_t)C::key(pr);
+    const u32 plx = C::idx(pl), prx = C::idx(pr);
+    u32 ma_prev = 0, mb_prev = 0, stg_prev = 0, ib_prev = 0;
     bool ok_prev = false;
-    u64 my_ra = 0, my_rb = 0; // pending reservation of the issuing thread
-    u32 ring = 0, ring_par = 0;   // stage and phase parity of tile i
+    u64 my_ra = 0, my_rb = 0;   // pending reservation of the issuing thread
+    u32 ring = 0, ring_par = 0; // stage and phase parity of tile i
     for (u64 i = 0; i <= my_n; ++i) {
         const bool cur = i < my_n, have_prev = i > 0;
         const u32 par = (u32)(i & 1), ppar = par ^ 1u;
-        u32 bal[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) bal[q] = 0;
-        u32 mb = 0, stg = 0, ib = 0;
+        u32 ma = 0, mb = 0, stg = 0, ib = 0;
         bool ok = false;
         if (cur) {
             stg = ring;
@@ -596,53 +607,47 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
             }
             ok = __all_sync(0xffffffffu, ok);
             // position of slot q = ib + (q / EPV) * STRIDE + q % EPV (32-bit: positions < 2^32)
-            ib = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE) + threadIdx.x * EPV;
+            const u32 tb = (u32)((blockIdx.x + i * gridDim.x) * (u64)Cfg::TILE);
+            ib = tb + threadIdx.x * EPV;
             if (ok) {
-                const unsigned char* mine = stages + (size_t)stg * Cfg::BYTES + threadIdx.x * 16u;
-                uint4 v[NV];
+                const u32 te = tb + Cfg::TILE - 1;
+                u32 le = 0;
+                if (!((plx >= tb && plx <= te) || (prx >= tb && prx <= te))) {
+                    // the tile holds neither pivot's position: ties with a
+                    // pivot's key are decided by the side it lies on
+                    raw_t rr[16];
+                    load_raw_stage<DT>(stages + (size_t)stg * Cfg::BYTES, rr);
+                    const bool ta = te < plx, tl = te <= prx;
+                    const RawBound<DT> ba = RawBound<DT>::le((key_t)(plk - (ta ? 0 : 1)));
+                    const RawBound<DT> bb = RawBound<DT>::le((key_t)(prk - (tl ? 0 : 1)));
+                    tile_masks_dispatch<DT>(rr, ba, bb, ta || plk != 0, tl || prk != 0, ma, le);
+                } else {
+                    key_t kk[16];
+                    InputSrc<DT>::template load16_smem<TMA_CONS>(
+                        reinterpret_cast<const uint4*>(stages + (size_t)stg * Cfg::BYTES), kk);
 #pragma unroll
-                for (int j = 0; j < NV; ++j) v[j] = *reinterpret_cast<const uint4*>(mine + j * (TMA_CONS * 16u));
-                raw_t rr[16];
-                InputSrc<DT>::unpack_raw(v, rr);
-                u32 hit = 0;
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const key_t kq = K::fwd(rr[q]);
-                    bal[q] = __ballot_sync(0xffffffffu, kq < plk);
-                    hit |= (u32)((key_t)(kq - plk) <= span) << q;
-                }
-                if (__any_sync(0xffffffffu, hit)) {
-                    // keys from the lower to the upper pivot's key: decide on the pair
-                    u32 ta = 0, m = hit;
-                    while (m) {
-                        const u32 q = (u32)(__ffs(m) - 1);
-                        m &= m - 1;
-                        const raw_t r = *reinterpret_cast<const raw_t*>(mine + slot_off(q));
-                        const ct c = C::make(K::fwd(r), ib + (q / EPV) * STRIDE + q % EPV);
-                        if (c < pl) ta |= 1u << q;
-                        else if (c <= pr) mb |= 1u << q;
-                    }
-                    if (__any_sync(0xffffffffu, ta)) {
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) bal[q] |= __ballot_sync(0xffffffffu, (ta >> q) & 1u);
+                    for (int q = 0; q < 16; ++q) {
+                        const ct c = C::make(kk[q], ib + (u32)((q / EPV) * STRIDE + q % EPV));
+                        ma |= (u32)(c < pl) << q;
+                        le |= (u32)(c <= pr) << q;
                     }
                 }
+                mb = le & ~ma;
             }
-            u32 wa = 0; // the same on every lane (sum of ballots)
-#pragma unroll
-            for (int q = 0; q < 16; ++q) wa += (u32)__popc(bal[q]);
+            const u32 wa = __reduce_add_sync(0xffffffffu, (u32)__popc(ma));
             const u32 wb = __reduce_add_sync(0xffffffffu, (u32)__popc(mb));
             if (lane == 0) {
                 ds.wa[par][warp] = wa;
                 ds.wb[par][warp] = wb;
             }
         }
-        Sync::sync(); // counts of tile i in; writes of tile i-2 done
+        // the issuer of tile i-1 publishes its reservation before the barrier
         const u32 issuer_cur = par ? 32u : 0u, issuer_prev = ppar ? 32u : 0u;
         if (have_prev && threadIdx.x == issuer_prev) {
             ds.ba[ppar] = my_ra;
             ds.bb[ppar] = my_rb;
         }
+        Sync::sync(); // counts of tile i, base of tile i-1 in; writes of tile i-2 done
         if (cur && threadIdx.x == issuer_cur) {
             u64 ta = 0, tb2 = 0;
             for (int w = 0; w < TMA_CONS / 32; ++w) {
@@ -656,30 +661,32 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
             if (ta) my_ra = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ta);
             if (tb2) my_rb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)tb2);
         }
-        Sync::sync(); // base of tile i-1 in
         if (have_prev && ok_prev) {
+            // this thread's element of slot q sits at a constant offset from `mine`
             const unsigned char* mine = stages + (size_t)stg_prev * Cfg::BYTES + threadIdx.x * 16u;
-            auto elem = [&](u32 q) -> raw_t { return *reinterpret_cast<const raw_t*>(mine + slot_off(q)); };
-            const u32 wa = ds.wa[ppar][warp];
-            if (wa) {
+            auto elem = [&](u32 q) -> raw_t {
+                return *reinterpret_cast<const raw_t*>(mine + (q / EPV) * (TMA_CONS * 16u) + (q % EPV) * sizeof(raw_t));
+            };
+            if (__any_sync(0xffffffffu, ma_prev)) {
                 const u64 xa = ds.ba[ppar] + ds.oa[ppar][warp];
-                if (xa + wa <= sink.cap_a) { // the usual case: no per-element bound
+                if (xa + ds.wa[ppar][warp] <= sink.cap_a) { // the usual case: no per-element bound
                     raw_t* okp = sink.out_keys + sink.out_base + xa;
                     u32* oip = sink.out_idx + sink.out_base + xa;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        // rank among the warp's selected elements of this slot;
-                        // the stores are predicated, the run pointers advance
-                        // by the slot's count (multiply-add unit)
-                        const u32 bq = bal_prev[q];
-                        const u32 r = (u32)__popc(bq & below);
+                        const bool bit = (ma_prev >> q) & 1u;
+                        const u32 bal = __ballot_sync(0xffffffffu, bit);
+                        // operands computed on every lane so that the stores
+                        // are predicated rather than branched around; the run
+                        // pointers advance by the slot's count
+                        const u32 r = (u32)__popc(bal & below);
                         const raw_t key = elem(q);
                         const u32 idx = ib_prev + (u32)((q / EPV) * STRIDE + q % EPV);
-                        if ((bq >> lane) & 1u) {
+                        if (bit) {
                             okp[r] = key;
                             oip[r] = idx;
                         }
-                        const u32 c = (u32)__popc(bq);
+                        const u32 c = (u32)__popc(bal);
                         okp += c;
                         oip += c;
                     }
@@ -687,15 +694,16 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
                     u64 ra = xa;
 #pragma unroll
                     for (int q = 0; q < 16; ++q) {
-                        const u32 bq = bal_prev[q];
-                        if ((bq >> lane) & 1u)
-                            sink.put_a_raw(ra + __popc(bq & below), elem(q),
+                        const bool bit = (ma_prev >> q) & 1u;
+                        const u32 bal = __ballot_sync(0xffffffffu, bit);
+                        if (bit)
+                            sink.put_a_raw(ra + __popc(bal & below), elem(q),
                                            ib_prev + (u32)((q / EPV) * STRIDE + q % EPV));
-                        ra += (u32)__popc(bq);
+                        ra += (u32)__popc(bal);
                     }
                 }
             }
-            if (ds.wb[ppar][warp]) { // b is sparse: each lane writes its own
+            if (__any_sync(0xffffffffu, mb_prev)) { // b is sparse: each lane writes its own
                 const u32 cnt = (u32)__popc(mb_prev);
                 u32 incl = cnt;
 #pragma unroll
@@ -714,8 +722,7 @@ __device__ void tma_consume_dense(const SelArgs& a, const SelState& s, const uns
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[stg_prev]); // stage may be refilled
         }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) bal_prev[q] = bal[q];
+        ma_prev = ma;
         mb_prev = mb;
         stg_prev = stg;
         ib_prev = ib;
@@ -749,6 +756,12 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     const SelState s = *a.st;
     if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT || (s.dense != 0) != DENSE) {
         grid_dep_release(); // the variant not needed lets the next launch proceed at once
+        return;
+    }
+    // the tile thresholds of the dense variant assume a window starting at the
+    // smallest pair, which holds on first levels (the only ones this kernel runs)
+    if (DENSE && Comp<KW>::from128(s.lo) != (typename Comp<KW>::t)0) {
+        if (threadIdx.x == 0) latch(a.err, ST_EINTERNAL);
         return;
     }
     // the working variant keeps the next kernel's blocks off its SMs until it ends
@@ -787,14 +800,8 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
         }
         return;
     }
-    typedef Comp<KW> C;
-    typedef typename C::t ct;
-    if (DENSE && C::from128(s.lo) != (ct)0) { // the dense variant runs on first levels only
-        if (threadIdx.x == 0) latch(a.err, ST_EINTERNAL);
-        return;
-    }
     WarpQ<KW>& q = wq[DENSE ? 0 : threadIdx.x >> 5];
-    if constexpr (!DENSE) tma_consume<DT, 0>(a, s, stages, full, empty, my_n, &dead, ps, q);
+    if constexpr (!DENSE) tma_consume_sparse<DT>(a, s, stages, full, empty, my_n, &dead, q);
     else tma_consume_dense<DT>(a, s, stages, full, empty, my_n, &dead, ds, ps);
     SyncNamed<1, TMA_CONS>::sync();
     if (threadIdx.x == 0) pass_epilogue(a);
@@ -1057,7 +1064,7 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     {
         double m = (double)n, kr = (double)k;
         while (m > tu.G && levels < 8) {
-            m = 1.5 * est_bracket((u64)m, (u64)std::max(1.0, std::min(kr, m)), tu.sample, tu.z);
+            m = 1.2 * est_bracket((u64)m, (u64)std::max(1.0, std::min(kr, m)), tu.sample, tu.z);
             kr = m / 2;
             ++levels;
         }

@@ -863,6 +863,32 @@ def run_probe_frequent(spec):
     return 0
 
 
+def run_probe_batched(spec):
+    """The 4096-row batched workload for profilers: THREADS:SPLIT (0 = the
+    default split length, -1 = none), two calls."""
+    import numpy as np
+    import torch
+    import paper_1502_03942_gb300 as tk
+    from paper_1502_03942_gb300 import workloads as wl
+    threads, split = (int(x) for x in spec.split(":"))
+    keys, off, ks = wl.batched_rows(4096, 10, 18, 1024, seed=4)
+    d_keys = torch.from_numpy(keys).cuda()
+    d_off = torch.from_numpy(off.view(np.int64)).cuda().view(torch.uint64)
+    d_k = torch.from_numpy(ks.view(np.int32)).cuda().view(torch.uint32)
+    ctx = tk.Context(0)
+    p = tk.make_params(block_threads=threads, sample_size=1024 if threads == 256 else 2048,
+                       split_rows=tk.TOPK_SPLIT_NONE if split < 0 else split)
+    res = tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=p)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=p, out=res[:4], out_off=res[4])
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"probe_batched": spec, "ms": e0.elapsed_time(e1), "status": ctx.sync()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -874,6 +900,8 @@ def main():
                     help="skip the plain, batched, sorted-runs and served measurements")
     ap.add_argument("--probe", default=None,
                     help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
+    ap.add_argument("--probe-batched", default=None,
+                    help="profiling aid: THREADS:SPLIT, two calls of topk_select_batched on 4096 rows")
     ap.add_argument("--probe-frequent", default=None,
                     help="profiling aid: ALG:LOG2N, two calls of topk_frequent (ec or pac)")
     args = ap.parse_args()
@@ -885,6 +913,8 @@ def main():
     __graft_entry__.build()
     if args.probe:
         return run_probe(args.probe)
+    if args.probe_batched:
+        return run_probe_batched(args.probe_batched)
     return run_ours(args)
 
 

@@ -90,6 +90,10 @@ typedef struct {
                                   capacity, and so the largest T, is 16, 8 or
                                   4 Ki composites of 32-bit keys for 1024,
                                   512 or 256 threads (half for u64) */
+    uint32_t split_rows;       /* topk_select_batched: rows longer than this
+                                  (and than T) take their first level over
+                                  the whole GPU instead of one block;
+                                  0xFFFFFFFF: no row does */
 } topk_params;
 
 /* Counters of the last completed call on a context (valid after
@@ -250,10 +254,17 @@ topk_status topk_runs_delete_min_flexible(topk_ctx *ctx, const void *d_keys,
  *              rank k_i.
  * Row lengths must be < 2^32.  Rows with bad k are reported by
  * topk_status_sync() as TOPK_EINVAL (their outputs are left untouched).
- * When params is NULL, or leaves block_threads, sample_size and
- * finish_threshold all zero, the choice remembered by topk_tune_batched for
- * this dtype and row count (power-of-two bucket) is used if there is one,
- * else 1024 threads, a 2048-element sample and the largest T. */
+ * Rows longer than the split length (params->split_rows, default 2^15)
+ * run their first recursion level over the whole GPU: one block draws the
+ * row's sample and pivots, one grid-wide pass classifies the tiles of all
+ * such rows, and the persistent kernel finishes them from their candidates
+ * (a fixed pool of 2^23 candidate pairs; a row it cannot hold is selected
+ * by one block).
+ * When params is NULL, or leaves block_threads, sample_size,
+ * finish_threshold and split_rows all zero, the choice remembered by
+ * topk_tune_batched for this dtype and row count (power-of-two bucket) is
+ * used if there is one, else 1024 threads, a 2048-element sample, the
+ * largest T and a split length of 2^15. */
 topk_status topk_select_batched(topk_ctx *ctx, const void *d_keys,
                                 const uint64_t *d_row_off, const uint32_t *d_row_k,
                                 uint32_t rows, topk_dtype dtype, void *d_out_keys,
@@ -326,9 +337,10 @@ topk_status topk_frequent(topk_ctx *ctx, const void *d_objects, uint64_t n, topk
 /* Autotuner of topk_select_batched (no counterpart in the paper): runs the
  * given batch with every candidate block size (256, 512, 1024 threads),
  * sample size (1024, 2048, 4096) and finish threshold (the block's capacity
- * and half of it), times each with CUDA events on `stream` (best of three
- * after one warm-up), and remembers the fastest for this dtype and row-count
- * bucket (floor(log2(rows))) in the context.  Arguments as
+ * and half of it), then with the fastest of those and every split length of
+ * 2^13, 2^15, 2^17 and none, times each with CUDA events on `stream` (best
+ * of three after one warm-up), and remembers the fastest for this dtype and
+ * row-count bucket (floor(log2(rows))) in the context.  Arguments as
  * topk_select_batched; every output is overwritten many times (the last run
  * uses the chosen setting, so the outputs are that call's result).
  *   base   NULL or settings copied into every candidate (seed, partitions,
@@ -343,9 +355,10 @@ topk_status topk_tune_batched(topk_ctx *ctx, const void *d_keys, const uint64_t 
                               void *d_kth_keys, uint32_t *d_kth_idx, const topk_params *base,
                               topk_params *best, void *stream);
 
-/* The autotuner's remembered choices as a text file: a header line, then one
- * line per entry: GPU name, dtype, row-count bucket, block_threads,
- * sample_size, finish_threshold, separated by tabs.  save writes every entry
+/* The autotuner's remembered choices as a text file: a header line
+ * ("topk-tuning 2"), then one line per entry: GPU name, dtype, row-count
+ * bucket, block_threads, sample_size, finish_threshold, split_rows, separated
+ * by tabs (files of version 1, without split_rows, are read too).  save writes every entry
  * of the context (TOPK_ECUDA if the file cannot be written); load adds the
  * entries whose GPU name matches this context's device and returns
  * TOPK_EINVAL for a missing or malformed file.  Host only; synchronous. */

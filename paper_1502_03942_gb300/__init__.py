@@ -41,7 +41,8 @@ class topk_params(ctypes.Structure):
     _fields_ = [("seed", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
                 ("sample_size", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
                 ("finish_threshold", ctypes.c_uint32), ("delta_factor", ctypes.c_float),
-                ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("split_rows", ctypes.c_uint32)]
 
 
 TOPK_FREQ_PAC = 0
@@ -204,9 +205,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+TOPK_SPLIT_NONE = 0xFFFFFFFF
+
+
 def make_params(seed=0, partitions=0, sample_size=0, finish_threshold=0, delta_factor=0.0,
-                flags=0, block_threads=0) -> topk_params:
-    return topk_params(seed, partitions, sample_size, 0, finish_threshold, delta_factor, flags, block_threads)
+                flags=0, block_threads=0, split_rows=0) -> topk_params:
+    return topk_params(seed, partitions, sample_size, 0, finish_threshold, delta_factor, flags, block_threads,
+                       split_rows)
 
 
 class Context:

@@ -27,8 +27,7 @@ template <int KW, int NT = BLK_NT, u32 CAP = Lim<KW>::ELEMS> struct BlockSmem {
     static constexpr int THREADS = NT;
     static constexpr u32 ELEMS = CAP;
     ct samp[CAP];
-    RadixSmem<KW, 2> rs2;
-    RadixSmem<KW, 1> rs1;
+    HistSelSmem<KW> hs;
     PassSmem<NT> ps;
     u32 kept;
     u32 flag;
@@ -171,10 +170,9 @@ template <int DT, class SM> __device__ void plan_level(const SelArgs& a, SM& sm,
             __syncthreads();
             const long long jl = sm.jl, jr = sm.jr;
             const long long top = (long long)kept - 1;
-            const u32 r[2] = {(u32)(jl < 0 ? 0 : jl > top ? top : jl), (u32)(jr < 0 ? 0 : jr > top ? top : jr)};
-            block_select_ranks<KW, 2>(sm.samp, kept, r, sm.rs2);
-            if (jl >= 0) pl = sm.rs2.result[0];
-            if (jr <= top) pr = sm.rs2.result[1];
+            const u32 r0 = (u32)(jl < 0 ? 0 : jl > top ? top : jl), r1 = (u32)(jr < 0 ? 0 : jr > top ? top : jr);
+            if (jl >= 0) pl = block_select_hist<KW, SM::THREADS>(sm.samp, kept, lo, hi, r0, sm.hs);
+            if (jr <= top) pr = block_select_hist<KW, SM::THREADS>(sm.samp, kept, lo, hi, r1, sm.hs);
         }
     }
     if (threadIdx.x == 0) {
@@ -247,9 +245,7 @@ template <int DT, class SM> __device__ void block_finish(const SelArgs& a, SM& s
         }
         return;
     }
-    const u32 r[1] = {(u32)(s.k_rem - 1)};
-    block_select_ranks<KW, 1>(sm.samp, count, r, sm.rs1);
-    const ct kth = sm.rs1.result[0];
+    const ct kth = block_select_hist<KW, NT>(sm.samp, count, lo, hi, (u32)(s.k_rem - 1), sm.hs);
     if (threadIdx.x == 0) sm.kept = 0;
     __syncthreads();
     raw_t* ok_out = static_cast<raw_t*>(a.out_keys);

@@ -105,6 +105,42 @@ template <int DT> struct InputSrc {
         unpack(v, kk);
     }
 
+    // The keys alone (positions from idx_of); bit s of the result = valid.
+    template <int NT> __device__ __forceinline__ u32 load16_keys(u64 base, key_t (&kk)[16]) const {
+        const u32 tid = threadIdx.x;
+        const u64 ext = extent();
+        if (base + (u64)NT * 16 <= ext) {
+            const uint4* p = reinterpret_cast<const uint4*>(keys) + base / EPV;
+            uint4 v[NV];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) v[j] = ld_stream(p + j * NT + tid);
+            unpack(v, kk);
+            u32 valid = 0xFFFFu;
+            if (base < head) { // the first tile: slots before the first key
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (base + (u64)((q / EPV) * NT + tid) * EPV + (q % EPV) < head) valid &= ~(1u << q);
+            }
+            return valid;
+        }
+        u32 valid = 0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+#pragma unroll
+            for (int i = 0; i < EPV; ++i) {
+                const u64 e = base + (u64)(j * NT + tid) * EPV + i;
+                const int q = j * EPV + i;
+                if (e >= head && e < ext) {
+                    kk[q] = K::fwd(keys[e]);
+                    valid |= 1u << q;
+                } else {
+                    kk[q] = 0;
+                }
+            }
+        }
+        return valid;
+    }
+
     // 16 elements per thread of the tile at tile coordinate `base`: slot
     // s = j*EPV + i is tile element base + (j*NT + tid)*EPV + i.  Bit s of the
     // returned mask = valid; ii receives positions.
@@ -1144,6 +1180,136 @@ __device__ typename Comp<KW>::t warp_select_rank(const typename Comp<KW>::t* v, 
         }
     }
     return prefix;
+}
+
+// ------------------------------------------------ selection by histogram
+// Block-wide selection of the element of 0-based rank `rank` among
+// v[0..count) (duplicates counted), all of which lie in the window [lo, hi]:
+// a histogram of 2^HS_BITS equal bins over the window (one pass, one shared
+// atomic per element), a prefix over the bins to find the bin holding the
+// rank, then either the bin's elements gathered and ranked by one warp
+// (warp_select_rank) or, for a larger bin, the window narrowed to that bin
+// and the step repeated.  A bin of width 1 holds copies of one composite, so
+// at most ceil(96 / HS_BITS) steps are taken.  Equivalent to sorting and
+// indexing; for sets that are spread over their window (samples, candidate
+// sets) it costs about two passes over them.
+constexpr u32 HS_BITS = 11;
+constexpr u32 HS_BINS = 1u << HS_BITS;
+constexpr u32 HS_GATHER = 512;
+
+template <int KW> struct HistSelSmem {
+    typedef typename Comp<KW>::t ct;
+    u32 hist[HS_BINS];
+    ct gath[HS_GATHER];
+    u32 whist[256];
+    u32 wsum[32];
+    ct wlo, whi, result;
+    u32 rank, bin, below, cnt, ng;
+};
+
+template <int KW, int NT>
+__device__ typename Comp<KW>::t block_select_hist(const typename Comp<KW>::t* v, u32 count, typename Comp<KW>::t lo,
+                                                   typename Comp<KW>::t hi, u32 rank, HistSelSmem<KW>& hs) {
+    typedef typename Comp<KW>::t ct;
+    static_assert(HS_BINS % NT == 0 && NT <= 1024, "bins per thread");
+    constexpr u32 PER = HS_BINS / NT; // consecutive bins per thread in the prefix
+    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    if (tid == 0) {
+        hs.wlo = lo;
+        hs.whi = hi;
+        hs.rank = rank;
+    }
+    __syncthreads();
+    for (int step = 0; step < 12; ++step) {
+        const ct wlo = hs.wlo, whi = hs.whi;
+        const int bl = bit_length_fast((ct)(whi - wlo));
+        const u32 sh = bl > (int)HS_BITS ? (u32)(bl - HS_BITS) : 0u;
+        auto bin_of = [&](ct c) -> u32 {
+            const ct d = (ct)(c - wlo) >> sh;
+            return d < (ct)HS_BINS ? (u32)d : HS_BINS - 1;
+        };
+        for (u32 i = tid; i < HS_BINS; i += NT) hs.hist[i] = 0;
+        __syncthreads();
+        for (u32 i = tid; i < count; i += NT) {
+            const ct c = v[i];
+            if (c >= wlo && c <= whi) atomicAdd(&hs.hist[bin_of(c)], 1u);
+        }
+        __syncthreads();
+        // the bin holding the rank: per-thread sums of PER bins, block scan
+        u32 h[PER], t = 0;
+#pragma unroll
+        for (u32 q = 0; q < PER; ++q) {
+            h[q] = hs.hist[tid * PER + q];
+            t += h[q];
+        }
+        u32 incl = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (u32)o) incl += y;
+        }
+        if (lane == 31) hs.wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const u32 x = lane < NT / 32 ? hs.wsum[lane] : 0u;
+            u32 wi = x;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const u32 y = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= (u32)o) wi += y;
+            }
+            if (lane < NT / 32) hs.wsum[lane] = wi - x;
+        }
+        __syncthreads();
+        const u32 r = hs.rank;
+        u32 run = hs.wsum[warp] + incl - t;
+#pragma unroll
+        for (u32 q = 0; q < PER; ++q) {
+            if (h[q] && r >= run && r < run + h[q]) {
+                hs.bin = tid * PER + q;
+                hs.below = run;
+                hs.cnt = h[q];
+            }
+            run += h[q];
+        }
+        if (tid == 0) hs.ng = 0;
+        __syncthreads();
+        const u32 b = hs.bin, cnt = hs.cnt, rr = r - hs.below;
+        if (cnt <= HS_GATHER) {
+            // the bin's elements, then one warp ranks them
+            for (u32 i0 = 0; i0 < count; i0 += NT) {
+                const u32 i = i0 + tid;
+                ct c = 0;
+                bool in = false;
+                if (i < count) {
+                    c = v[i];
+                    in = c >= wlo && c <= whi && bin_of(c) == b;
+                }
+                const u32 bal = __ballot_sync(0xffffffffu, in);
+                u32 base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&hs.ng, (u32)__popc(bal));
+                base = __shfl_sync(0xffffffffu, base, 0) + (u32)__popc(bal & lanemask_lt());
+                if (in && base < HS_GATHER) hs.gath[base] = c;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const ct res = warp_select_rank<KW>(hs.gath, cnt, rr, hs.whist);
+                if (lane == 0) hs.result = res;
+            }
+            __syncthreads();
+            return hs.result;
+        }
+        // a large bin: narrow the window to it and repeat
+        if (tid == 0) {
+            const ct nlo = (ct)(wlo + ((ct)b << sh));
+            const ct top = (ct)(nlo + (((ct)1 << sh) - 1));
+            hs.wlo = nlo;
+            hs.whi = (b == HS_BINS - 1 || top > whi) ? whi : top;
+            hs.rank = rr;
+        }
+        __syncthreads();
+    }
+    return hs.wlo; // not reached: each step narrows the window by 2^HS_BITS
 }
 
 // ------------------------------------------------------------- sampling

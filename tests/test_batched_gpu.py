@@ -1,8 +1,10 @@
 """topk_select_batched on the GPU against the CPU oracle (bit-exact per row).
 
 Rows of uneven length at arbitrary (unaligned) offsets, each with its own k,
-in one persistent launch; every key type; the full batched configuration
-(4096 rows, lengths 2^U(10,18), N(0,3) keys, k in 1..1024) checked against the
+in one persistent launch; every key type; rows longer than the split length
+("wide" rows, whose first level runs over the whole GPU) at several split
+lengths, with heavy ties and large k; the full batched configuration (4096
+rows, lengths 2^U(10,18), N(0,3) keys, k in 1..1024) checked against the
 oracle on a sample of rows and by properties on all rows.
 """
 import numpy as np
@@ -162,9 +164,11 @@ def test_tuner_choice_and_file(tk, tmp_path):
     path = tmp_path / "tuning.txt"
     tk.topk_tuning_save(c1, str(path))
     lines = path.read_text().splitlines()
-    assert lines[0] == "topk-tuning 1" and len(lines) == 2
+    assert lines[0] == "topk-tuning 2" and len(lines) == 2
     fields = lines[1].split("\t")
-    assert fields[3:] == [str(best.block_threads), str(best.sample_size), str(best.finish_threshold)]
+    assert fields[3:] == [str(best.block_threads), str(best.sample_size), str(best.finish_threshold),
+                          str(best.split_rows)]
+    assert best.split_rows in (1 << 13, 1 << 15, 1 << 17, tk.TOPK_SPLIT_NONE)
     c2 = tk.Context(0)
     tk.topk_tuning_load(c2, str(path))
     path2 = tmp_path / "tuning2.txt"
@@ -177,3 +181,51 @@ def test_tuner_choice_and_file(tk, tmp_path):
     assert e.value.status == tk.TOPK_EINVAL
     c1.close()
     c2.close()
+
+
+@pytest.mark.parametrize("name", ["u32", "i32", "f32", "bf16", "u64"])
+def test_wide_rows(tk, ctx, name):
+    """Rows of 2^12 .. 2^17 keys at unaligned offsets with split lengths that
+    make most (4096), some (2^15) or none of them wide: every row the
+    oracle's, whichever path it took; k up to 4096 and some rows at n/2."""
+    keys, off, ks = rows_for(name, 48, 12, 17, 4096, seed=47)
+    lens = np.diff(off).astype(np.int64)
+    ks[::5] = (lens[::5] // 2).astype(np.uint32)
+    d_keys, d_off, d_k = to_device(keys, name), to_device(off, "u64"), to_device(ks, "u32")
+    for split in (4096, 1 << 15, tk.TOPK_SPLIT_NONE):
+        res = tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=tk.make_params(split_rows=split))
+        check_rows(keys, off, ks, name, res, range(48))
+
+
+@pytest.mark.parametrize("name", ["f32", "u64"])
+def test_wide_rows_heavy_ties(tk, ctx, name):
+    """Wide rows over a handful of values: the pivots fall inside runs of
+    equal keys, so positions decide, in the grid pass and in the finish."""
+    g = np.random.Generator(np.random.Philox(48))
+    lens = np.floor(2.0 ** g.uniform(14, 17, size=24)).astype(np.uint64)
+    off = np.zeros(25, np.uint64)
+    off[1:] = np.cumsum(lens)
+    vals = g.integers(0, 5, size=int(off[-1]))
+    if name == "f32":
+        keys = np.array([-1.0, -0.0, 0.0, 2.5, np.inf], np.float32)[vals].view(np.uint32)
+    else:
+        keys = vals.astype(np.uint64) * np.uint64(0x1234_5678_9ABC)
+    ks = np.minimum(g.integers(1, 20000, size=24), lens).astype(np.uint32)
+    d_keys, d_off, d_k = to_device(keys, name), to_device(off, "u64"), to_device(ks, "u32")
+    res = tk.topk_select_batched(ctx, d_keys, d_off, d_k, params=tk.make_params(split_rows=4096))
+    check_rows(keys, off, ks, name, res, range(24))
+
+
+def test_tuning_file_version_1_is_read(tk, tmp_path):
+    """A tuning file written before the split length existed still loads (its
+    entries then choose the split length automatically)."""
+    import torch
+    name = torch.cuda.get_device_name(0)
+    path = tmp_path / "v1.txt"
+    path.write_text(f"topk-tuning 1\n{name}\t2\t8\t256\t1024\t4096\n")
+    c = tk.Context(0)
+    tk.topk_tuning_load(c, str(path))
+    out = tmp_path / "v2.txt"
+    tk.topk_tuning_save(c, str(out))
+    assert out.read_text().splitlines()[1].split("\t")[3:] == ["256", "1024", "4096", "0"]
+    c.close()

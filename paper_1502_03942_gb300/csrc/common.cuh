@@ -211,6 +211,7 @@ struct SelArgs {
     u32* hist;                // HIST_BINS bins over the window (zero between levels)
     u32* pass_done;           // block-done counter of the pass (zero between passes)
     u32 samp_cap;
+    u32* gbar;                // one-launch path: grid barrier words (arrivals, generation)
 };
 
 // Largest composite of a key type's domain (the first window's upper end):

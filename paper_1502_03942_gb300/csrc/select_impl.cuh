@@ -807,6 +807,158 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     if (threadIdx.x == 0) pass_epilogue(a);
 }
 
+// ---- one-launch selection of a small input: the first level's steps in
+// one cooperative kernel of one block per SM, separated by a bounded grid
+// barrier, then the exact finish in block 0.  For inputs of up to SMALL_MAX
+// keys the separate launches of the grid levels cost more than their work.
+constexpr u64 SMALL_MAX = 1ull << 22;
+constexpr int SMALL_NT = 512;
+constexpr u64 GRID_BARRIER_NS = 200ull * 1000 * 1000;
+template <int KW> using SmallSmem = BlockSmem<KW, SMALL_NT>;
+
+// Every block of the grid arrives, then waits (at most `limit_ns`) until all
+// have: words[0] counts arrivals and is reset by the last one, which then
+// advances the generation words[1].  False after a timeout.
+__device__ __forceinline__ bool grid_barrier(u32* words, u64 limit_ns) {
+    __shared__ u32 s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile u32* gen = words + 1;
+        const u32 g0 = *gen;
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(words, 1u) == gridDim.x - 1) {
+            atomicExch(words, 0u);
+            __threadfence();
+            atomicAdd(words + 1, 1u);
+        } else {
+            u64 t0, t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (*gen == g0) {
+                __nanosleep(64);
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > limit_ns) {
+                    ok = false;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int DT> __global__ void __launch_bounds__(SMALL_NT, 1) k_small(SelArgs a) {
+    typedef Key<DT> K;
+    typedef typename K::raw_t raw_t;
+    typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<SmallSmem<KW>*>(smem_raw);
+    SelState* g = a.st;
+    const u32 tid = threadIdx.x;
+    const u32 m = (u32)a.n;
+    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, a.n);
+    // 1. the sample: draw j falls in partition j mod p (an equal share per
+    //    partition) at a position uniform in it (Philox4x32-10 word j mod 4 of
+    //    counter (j / 4, 0, salt, 0)); every draw lies in the first window
+    const u32 s = a.sample;
+    const u32 p = a.parts < m ? a.parts : m;
+    const u32 len = m / p, rem = m - len * p;
+    ct* samp = static_cast<ct*>(a.samp);
+    for (u32 j = blockIdx.x * SMALL_NT + tid; j < s; j += gridDim.x * SMALL_NT) {
+        const Philox4 r = philox4x32_10(j >> 2, 0, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
+        const u32 part = j % p;
+        const u32 plo = part * len + (part < rem ? part : rem);
+        const u32 psz = len + (part < rem ? 1 : 0);
+        const u32 pos = plo + (u32)(((u64)r.v[j & 3] * psz) >> 32);
+        key_t kq;
+        u32 x;
+        isrc.at(pos, kq, x);
+        samp[j] = C::make(kq, x);
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        *g = initial_state<DT>(a);
+        g->phase = PH_RUN;
+    }
+    if (!grid_barrier(a.gbar, GRID_BARRIER_NS)) {
+        if (tid == 0) latch(a.err, ST_ETIMEOUT);
+        return;
+    }
+    // 2. the pivots, in every block alike: the sample elements of ranks
+    //    k|S|/n -/+ Delta (the same rule as the grid levels)
+    {
+        // the whole sample into shared memory, 16-byte loads, all in flight
+        // (s * sizeof(ct) is a multiple of 16 bytes: s is at least 64)
+        constexpr u32 PER = (Lim<KW>::ELEMS * sizeof(ct) / 16 + SMALL_NT - 1) / SMALL_NT;
+        const uint4* src4 = reinterpret_cast<const uint4*>(samp);
+        uint4* dst4 = reinterpret_cast<uint4*>(sm.samp);
+        const u32 n4 = (u32)((s * sizeof(ct)) / 16);
+        uint4 v[PER];
+#pragma unroll
+        for (u32 q = 0; q < PER; ++q) {
+            const u32 i = q * SMALL_NT + tid;
+            if (i < n4) v[q] = __ldcg(src4 + i);
+        }
+#pragma unroll
+        for (u32 q = 0; q < PER; ++q) {
+            const u32 i = q * SMALL_NT + tid;
+            if (i < n4) dst4[i] = v[q];
+        }
+    }
+    if (tid == 0) {
+        long long jl, jr;
+        pivot_ranks(s, a.n, a.k, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+        sm.jl = jl;
+        sm.jr = jr;
+    }
+    __syncthreads();
+    const ct lo = 0, hi = C::from128(key_domain_max<DT>());
+    const long long jl = sm.jl, jr = sm.jr, top = (long long)s - 1;
+    ct pl = lo, pr = hi;
+    if (jl >= 0) pl = block_select_hist<KW, SMALL_NT>(sm.samp, s, lo, hi, (u32)(jl > top ? top : jl), sm.hs);
+    if (jr <= top) pr = block_select_hist<KW, SMALL_NT>(sm.samp, s, lo, hi, (u32)(jr < 0 ? 0 : jr), sm.hs);
+    // 3. the pass: a to the output, b to the candidate buffer
+    {
+        Sink<DT> sink;
+        sink.out_keys = static_cast<raw_t*>(a.out_keys);
+        sink.out_idx = a.out_idx;
+        sink.out_base = 0;
+        sink.cap_a = a.k;
+        sink.ck = static_cast<key_t*>(a.cand_key[0]);
+        sink.ci = a.cand_idx[0];
+        sink.cap_b = a.cap_b;
+        sink.cnt_a = &g->cnt_a;
+        sink.cnt_b = &g->cnt_b;
+        if (pl > lo) pass_tiles<SMALL_NT, true, false, DT>(isrc, blockIdx.x, gridDim.x, lo, pl, pr, sink, sm.ps);
+        else pass_tiles<SMALL_NT, false, false, DT>(isrc, blockIdx.x, gridDim.x, lo, pl, pr, sink, sm.ps);
+    }
+    if (!grid_barrier(a.gbar, GRID_BARRIER_NS)) {
+        if (tid == 0) latch(a.err, ST_ETIMEOUT);
+        return;
+    }
+    // 4. block 0: the branch of Algorithm "select", then the finish
+    if (blockIdx.x != 0) return;
+    if (tid == 0) {
+        g->pl = (u128)pl;
+        g->pr = (u128)pr;
+        g->dst = SRC_CAND0;
+        g->pending = 1;
+        g->level = 1;
+        g->levels_grid = 1;
+        g->sample_kept = s;
+        g->cnt_a = *(volatile u64*)&g->cnt_a;
+        g->cnt_b = *(volatile u64*)&g->cnt_b;
+        decide(*g);
+    }
+    __syncthreads();
+    block_levels_and_finish<DT, true, true>(a, sm);
+}
+
 // Remaining levels in one block, then the exact finish.
 template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, int first) {
     grid_dep_wait();
@@ -997,7 +1149,9 @@ template <int DT> static topk_status set_smem_attrs() {
     if (cudaFuncSetAttribute(k_pivots<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PivotSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
-    if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
+        cudaFuncSetAttribute(k_small<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SmallSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
     done_mask.fetch_or(bit);
     return TOPK_OK;
@@ -1026,6 +1180,23 @@ template <int DT> static int pass_grid(int sms, bool first) {
         occ_first = std::max(1, o1);
     }
     return sms * (first ? occ_first : occ_rest);
+}
+
+// Whether one block of k_small fits on every SM (the cooperative launch
+// needs the whole grid resident).
+template <int DT> static bool small_fits(int sms) {
+    static int occ = -1;
+    if (occ < 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_small<DT>, SMALL_NT, sizeof(SmallSmem<Key<DT>::KW>)) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            o = 0;
+        }
+        occ = o;
+    }
+    (void)sms;
+    return occ >= 1;
 }
 
 // Candidate capacity for a first level over n keys: twice the expected
@@ -1059,6 +1230,20 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     }
     topk_status rs = set_smem_attrs<DT>();
     if (rs != TOPK_OK) return rs;
+    // the first level's expected bracket fits the finishing block
+    if (n <= SMALL_MAX && n > tu.G && a.gbar != nullptr && (!ctx || ctx->one_launch) && small_fits<DT>(sms) &&
+        1.2 * est_bracket(n, k, tu.sample, tu.z) <= (double)tu.T) {
+        // one launch: sample, pivots, pass and finish (cooperative, one block per SM)
+        if (ctx) profile_pass_begin(ctx, st);
+        cudaError_t e = cudaMemsetAsync(a.gbar, 0, 2 * sizeof(u32), st);
+        if (e == cudaSuccess) e = launch_coop(k_small<DT>, sms, SMALL_NT, sizeof(SmallSmem<KW>), st, a);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (ctx) {
+            profile_pass_end(ctx, st);
+            count_launch(ctx);
+        }
+        return cuda_status(cudaGetLastError());
+    }
     // grid levels until the candidates fit the block finisher's range
     int levels = 0;
     {
@@ -1133,6 +1318,7 @@ topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_
     a.samp_cap = Lim<KW>::ELEMS;
     a.samp_count = ctx->d_counter + 3;
     a.pass_done = ctx->d_counter + 2;
+    a.gbar = ctx->d_counter + 8;
     a.hist = ctx->d_hist;
     a.cand_key[0] = base + off_k0;
     a.cand_key[1] = base + off_k1;
@@ -1177,6 +1363,7 @@ template <int DT> topk_status noalloc_prepare_dt(int sms) {
     (void)tma_grid<DT, false>(sms);
     (void)tma_grid<DT, true>(sms);
     (void)pass_grid<DT>(sms, true);
+    (void)small_fits<DT>(sms);
     return cudaGetLastError() == cudaSuccess ? TOPK_OK : TOPK_ECUDA;
 }
 
@@ -1203,6 +1390,7 @@ topk_status run_select_noalloc(char* base, int sms, const void* keys, u64 n, u64
     a.samp_cap = Lim<KW>::ELEMS;
     a.pass_done = words + 2;
     a.samp_count = words + 3;
+    a.gbar = words + 8;
     a.hist = reinterpret_cast<u32*>(base + NA_OFF_HIST);
     // the error word, the block-done counters, the sample count and the
     // histogram must start at zero (a call that failed may have left them set)

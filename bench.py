@@ -50,7 +50,7 @@ def measured_peaks():
 
 # the sources the first-level pass is compiled from (its traffic record is
 # valid while these are unchanged)
-FIRST_PASS_SOURCES = ("common.cuh", "select.cu", "select_block.cuh", "select_core.cuh")
+FIRST_PASS_SOURCES = ("common.cuh", "select.cu", "select_block.cuh", "select_core.cuh", "select_impl.cuh")
 
 
 def source_hash():
@@ -212,6 +212,44 @@ def host_info():
     import platform
     return {"nproc": os.cpu_count(), "cores": cores, "cpu_model": model or "unknown",
             "arch": platform.machine()}
+
+
+class numa_local:
+    """Within the block, the process runs on the CPUs of the GPU's own NUMA
+    node (from sysfs), so that pinned host buffers allocated there are local
+    to the GPU; the previous CPU set is restored afterwards.  Does nothing
+    where sysfs gives no node."""
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.saved = None
+
+    def _cpus(self):
+        import torch
+        pr = torch.cuda.get_device_properties(self.device_index)
+        bus = f"{pr.pci_domain_id:04x}:{pr.pci_bus_id:02x}:{pr.pci_device_id:02x}.0"
+        node = int(open(f"/sys/bus/pci/devices/{bus}/numa_node").read().strip())
+        if node < 0:
+            return None
+        cpus = set()
+        for part in open(f"/sys/devices/system/node/node{node}/cpulist").read().strip().split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus or None
+
+    def __enter__(self):
+        try:
+            cpus = self._cpus()
+            if cpus:
+                self.saved = os.sched_getaffinity(0)
+                os.sched_setaffinity(0, cpus)
+        except Exception:
+            self.saved = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.saved is not None:
+            os.sched_setaffinity(0, self.saved)
 
 
 def time_oracle(host_keys, budget_s=20.0, slice_n=1 << 22, threads=None):
@@ -742,28 +780,63 @@ def run_ours(args):
                                    "frac_of_hbm": gbs / peak, "grid_levels": stt["levels_grid"],
                                    "first_candidates": stt["first_candidates"]}
 
-    # end to end: pinned host input -> device, select, outputs -> host
+    # end to end: pinned host input -> device, select, outputs -> host.  The
+    # next dataset's input is copied on its own stream while the current one
+    # is selected (two device input buffers), and each dataset's outputs go
+    # back on a third stream while the next dataset is selected; pinned
+    # buffers are allocated from CPUs on the GPU's own NUMA node.
     e2e = None
     if True:  # every rank: the timing is max-reduced across ranks
-        host = {ds: torch.empty(N, dtype=torch.float32, pin_memory=True) for ds in DATASETS}
+        with numa_local(local):
+            host = {ds: torch.empty(N, dtype=torch.float32, pin_memory=True) for ds in DATASETS}
+            hout = {(ds, k): tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs[k])
+                    for ds in DATASETS for k in KS}
         for ds in DATASETS:
             host[ds].copy_(data[ds])
-        dev = torch.empty(N, dtype=torch.float32, device="cuda")
-        hout = {k: tuple(torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in outs[k]) for k in KS}
+        dev = [torch.empty(N, dtype=torch.float32, device="cuda") for _ in range(2)]
+        douts = {(ds, k): tuple(torch.empty_like(t) for t in outs[k]) for ds in DATASETS for k in KS}
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
         h2d = 3 * N * 4
         d2h = sum(k * 8 + 8 for k in KS) * len(DATASETS)
         steps_e2e = max(1, min(args.steps, 3))
 
+        freed = [None, None]            # selections done with input buffer b
+        copied = {ds: None for ds in DATASETS}  # dataset's outputs back on the host
+
         def e2e_step():
-            for ds in DATASETS:
-                dev.copy_(host[ds], non_blocking=True)
+            for i, ds in enumerate(DATASETS):
+                b = i % 2
+                buf = dev[b]
+                with torch.cuda.stream(s_in):
+                    if freed[b] is not None:
+                        s_in.wait_event(freed[b])
+                    buf.copy_(host[ds], non_blocking=True)
+                    arrived = torch.cuda.Event()
+                    arrived.record(s_in)
+                stream.wait_event(arrived)
+                if copied[ds] is not None:
+                    stream.wait_event(copied[ds])
                 for k in KS:
-                    tk.topk_select(ctx, dev, k, params=params, out=outs[k], check=False, stream=stream)
-                    for h, d in zip(hout[k], outs[k]):
-                        h.copy_(d, non_blocking=True)
+                    tk.topk_select(ctx, buf, k, params=params, out=douts[(ds, k)], check=False, stream=stream)
+                freed[b] = torch.cuda.Event()
+                freed[b].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(freed[b])
+                    for k in KS:
+                        for h, d in zip(hout[(ds, k)], douts[(ds, k)]):
+                            h.copy_(d, non_blocking=True)
+                    copied[ds] = torch.cuda.Event()
+                    copied[ds].record(s_out)
 
         e2e_step()
         torch.cuda.synchronize()
+        # the host link alone: one pinned 1 GiB copy to the device
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        dev[0].copy_(host[DATASETS[0]], non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link_gbs = N * 4 / (l0.elapsed_time(l1) / 1e3) / 1e9
         barrier()
         t0 = time.perf_counter()
         for _ in range(steps_e2e):
@@ -772,7 +845,10 @@ def run_ours(args):
         t_e2e = time.perf_counter() - t0
         t_e2e = max_over_ranks(t_e2e, dist, "cuda")
         e2e = {"value": world * steps_e2e * len(DATASETS) * len(KS) * N / t_e2e, "unit": "keys/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "h2d_GBps_achieved": steps_e2e * h2d / t_e2e / 1e9, "h2d_link_GBps": link_gbs,
+               "overlap": "H2D of the next dataset and D2H of the last one's outputs run beside the selections"}
+        del host, hout, dev, douts
 
     if rank != 0:
         if dist is not None:
@@ -863,6 +939,25 @@ def run_probe_frequent(spec):
     return 0
 
 
+def run_probe_runs(spec):
+    """Multisequence selection for profilers: K (1024 sorted u64 runs of
+    2^U(10,20) keys; "half" for total/2), two calls."""
+    import numpy as np
+    import torch
+    import paper_1502_03942_gb300 as tk
+    from paper_1502_03942_gb300 import workloads as wl
+    keys, off = wl.sorted_runs(1024, 10, 20, seed=3)
+    d_keys = torch.from_numpy(keys.view(np.int64)).cuda().view(torch.uint64)
+    d_off = torch.from_numpy(off.view(np.int64)).cuda().view(torch.uint64)
+    k = int(off[-1]) // 2 if spec == "half" else int(spec)
+    ctx = tk.Context(0)
+    out = tk.topk_select_sorted_runs(ctx, d_keys, d_off, k)
+    tk.topk_select_sorted_runs(ctx, d_keys, d_off, k, out=out)
+    torch.cuda.synchronize()
+    print(json.dumps({"probe_runs": spec, "stats": ctx.last_stats()}))
+    return 0
+
+
 def run_probe_batched(spec):
     """The 4096-row batched workload for profilers: THREADS:SPLIT (0 = the
     default split length, -1 = none), two calls."""
@@ -900,6 +995,8 @@ def main():
                     help="skip the plain, batched, sorted-runs and served measurements")
     ap.add_argument("--probe", default=None,
                     help="profiling aid: DATASET:N:K[:FLAGS], one warm-up and one timed-by-profiler call")
+    ap.add_argument("--probe-runs", default=None,
+                    help="profiling aid: K or 'half', two multisequence selections over 1024 sorted runs")
     ap.add_argument("--probe-batched", default=None,
                     help="profiling aid: THREADS:SPLIT, two calls of topk_select_batched on 4096 rows")
     ap.add_argument("--probe-frequent", default=None,
@@ -915,6 +1012,8 @@ def main():
         return run_probe(args.probe)
     if args.probe_batched:
         return run_probe_batched(args.probe_batched)
+    if args.probe_runs:
+        return run_probe_runs(args.probe_runs)
     return run_ours(args)
 
 

@@ -578,7 +578,7 @@ def measure_frequent(tk, wl, torch, ctx, peak_gbs):
     return res
 
 
-def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
+def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5, budget=64 << 30, per_call=True):
     """Poisson arrivals at `rate`/s for `seconds`: n = 2^U(10,26), u32 or bf16,
     uniform or Zipf (s=1.2, 10^4 values), k = 2^U(0, log2(n/4)); 64 GB budget.
     Inputs come from a pool of distinct device arrays; outputs from a ring
@@ -656,7 +656,7 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     kth = (base + phys + kb + 4 * k_arr + 15) & ~15
     reqs["d_kth_key"] = kth
     reqs["d_kth_idx"] = kth + 16
-    srv = tk.Server(0, hbm_budget=64 << 30, max_slots=16)
+    srv = tk.Server(0, hbm_budget=budget, max_slots=16)
     t0 = srv.now_ns() + 20_000_000
     reqs["arrival_ns"] = t0 + np.cumsum((gaps * 1e9).astype(np.int64))
     tickets, lags = srv.replay(reqs, done_before)
@@ -665,6 +665,18 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     st = srv.stats()
     srv.close()
     offered_keys = sum(pool[which[i]].numel() for i in range(count))
+    served_s = st["elapsed_s"]
+    res = {"workload": f"Poisson {rate:.0f} req/s for {seconds} s, n=2^U(10,26) u32|bf16 uniform|Zipf, "
+                       f"k=2^U(0,log2(n/4)), {budget / 2**30:.0f} GiB budget, 16 slots",
+           "requests": count, "failed": bad + st["failed"], "p50_ms": st["p50_ns"] / 1e6,
+           "p99_ms": st["p99_ns"] / 1e6, "keys_per_s": st["keys"] / served_s if served_s else None,
+           "offered_keys_per_s": offered_keys / seconds, "batched_requests": st["batched_requests"],
+           "batches": st["batches"], "peak_inflight_GB": st["peak_inflight_bytes"] / 1e9,
+           "budget_GB": budget / 1e9, "slots_reserved_GB": st["reserved_bytes"] / 1e9,
+           "budget_waits": st["budget_waits"],
+           "served_s": served_s, "submit_lag_p99_ms": float(np.percentile(lags, 99)) / 1e6}
+    if not per_call:
+        return res
     # the same requests, one launch sequence per request, back to back
     ctx = tk.Context(0)
     outs = {}
@@ -681,16 +693,8 @@ def measure_served(tk, wl, torch, seconds=10.0, rate=20000.0, seed=5):
     torch.cuda.synchronize()
     per_call_s = e0.elapsed_time(e1) / 1e3
     ctx.close()
-    served_s = st["elapsed_s"]
-    return {"workload": f"Poisson {rate:.0f} req/s for {seconds} s, n=2^U(10,26) u32|bf16 uniform|Zipf, "
-                        "k=2^U(0,log2(n/4)), 64 GB budget, 16 slots",
-            "requests": count, "failed": bad + st["failed"], "p50_ms": st["p50_ns"] / 1e6,
-            "p99_ms": st["p99_ns"] / 1e6, "keys_per_s": st["keys"] / served_s if served_s else None,
-            "offered_keys_per_s": offered_keys / seconds, "batched_requests": st["batched_requests"],
-            "batches": st["batches"], "peak_inflight_GB": st["peak_inflight_bytes"] / 1e9,
-            "per_call_keys_per_s": offered_keys / per_call_s, "per_call_s": per_call_s,
-            "served_s": served_s,
-            "submit_lag_p99_ms": float(np.percentile(lags, 99)) / 1e6}
+    res.update({"per_call_keys_per_s": offered_keys / per_call_s, "per_call_s": per_call_s})
+    return res
 
 
 # --------------------------------------------------------------- GPU arm
@@ -887,7 +891,9 @@ def run_ours(args):
                         ("batched", lambda: measure_batched(tk, wl, torch, ctx)),
                         ("sorted_runs", lambda: measure_sorted_runs(tk, wl, torch, ctx)),
                         ("frequent", lambda: measure_frequent(tk, wl, torch, ctx, peak)),
-                        ("served", lambda: measure_served(tk, wl, torch))):
+                        ("served", lambda: measure_served(tk, wl, torch)),
+                        ("served_pressure", lambda: measure_served(tk, wl, torch, seconds=4.0, budget=1 << 29,
+                                                                   per_call=False))):
             try:
                 line[key] = fn()
             except Exception as e:  # reported in the line, never hides the main metric

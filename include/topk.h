@@ -431,14 +431,23 @@ typedef struct {
     uint64_t batched_requests;
     uint64_t peak_inflight_bytes;
     double elapsed_s;       /* first arrival to last completion */
+    uint64_t reserved_bytes; /* device memory the server's slots hold beside
+                                the budget: each slot's scratch (sized at
+                                creation for a 2^26-key selection and a
+                                2048-row batch, grown by larger requests),
+                                its fixed words and pointer arrays */
+    uint64_t budget_waits;  /* requests that reached the head of the queue
+                               and had to wait for room in the budget */
 } topk_serve_report;
 
 /* Creates a server on `device` with `max_slots` streams (1..64) and a
  * budget in bytes.  Starts the server's worker thread.  Every slot owns a
  * context whose scratch is reserved up front for a selection of 2^26 64-bit
  * keys and a batch of 2048 rows (about 0.6 GiB per slot, outside the
- * budget), so that serving seldom allocates; larger requests grow it on first
- * use.  TOPK_ENOMEM if that memory is not available. */
+ * budget, which covers the requests' own inputs, outputs and state), so that
+ * serving seldom allocates; larger requests grow it on first use.
+ * topk_serve_stats reports what the slots hold as reserved_bytes.
+ * TOPK_ENOMEM if that memory is not available. */
 topk_status topk_serve_create(topk_server **out, int device, uint64_t hbm_budget,
                               uint32_t max_slots);
 

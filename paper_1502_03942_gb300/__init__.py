@@ -73,7 +73,8 @@ class topk_serve_report(ctypes.Structure):
                 ("rejected", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("keys", ctypes.c_uint64),
                 ("p50_ns", ctypes.c_uint64), ("p99_ns", ctypes.c_uint64), ("max_ns", ctypes.c_uint64),
                 ("batches", ctypes.c_uint64), ("batched_requests", ctypes.c_uint64),
-                ("peak_inflight_bytes", ctypes.c_uint64), ("elapsed_s", ctypes.c_double)]
+                ("peak_inflight_bytes", ctypes.c_uint64), ("elapsed_s", ctypes.c_double),
+                ("reserved_bytes", ctypes.c_uint64), ("budget_waits", ctypes.c_uint64)]
 
 
 _lib = None

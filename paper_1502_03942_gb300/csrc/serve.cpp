@@ -32,6 +32,7 @@ using topk::BATCH_ROW_MAX;
 constexpr uint32_t MAX_BATCH_ROWS = 2048;
 constexpr uint64_t RESERVE_N = 1ull << 26;  // selection size each slot's scratch is reserved for
 constexpr uint64_t REQUEST_OVERHEAD = 4096; // state and bookkeeping per request
+constexpr uint64_t CTX_FIXED_BYTES = 256 + 64 * 4 + 4096 + 4096 * 4; // a context's error word, counters, state, histogram
 
 uint64_t steady_ns() {
     return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -44,6 +45,7 @@ struct Pending {
     uint64_t ticket;
     uint64_t bytes;
     uint64_t arrival;
+    bool budget_wait = false; // counted once when it first waited for room in the budget
 };
 
 struct Slot {
@@ -56,7 +58,16 @@ struct Slot {
     char* h_ptrs = nullptr; // pinned staging of the batched pointer arrays
     char* d_ptrs = nullptr;
     uint32_t* h_err = nullptr; // pinned copy of the context's error word, read after each dispatch
+    uint64_t held = 0;         // device bytes the slot holds outside any request
 };
+
+// Device memory a slot holds outside the requests' own buffers: its
+// context's scratch blocks and fixed words, and the batched pointer arrays.
+uint64_t slot_held(const Slot& slot) {
+    const topk_ctx* c = slot.ctx;
+    if (!c) return 0;
+    return (uint64_t)c->scratch.bytes + c->freq.bytes + c->aux.bytes + CTX_FIXED_BYTES + 52ull * MAX_BATCH_ROWS;
+}
 
 uint64_t request_bytes(const topk_request& r) {
     const int w = topk::dtype_bytes(r.dtype);
@@ -164,7 +175,13 @@ void worker_main(topk_server* s) {
                 if (slot.busy) continue;
                 if (s->queue.empty()) break;
                 Pending& head = s->queue.front();
-                if (s->inflight + head.bytes > s->budget) break; // FIFO: wait for room
+                if (s->inflight + head.bytes > s->budget) { // FIFO: wait for room
+                    if (!head.budget_wait) {
+                        head.budget_wait = true;
+                        s->st.budget_waits++;
+                    }
+                    break;
+                }
                 const bool small = head.r.n <= BATCH_ROW_MAX;
                 const topk_dtype dt = head.r.dtype;
                 do {
@@ -193,6 +210,12 @@ void worker_main(topk_server* s) {
         }
         for (Slot* slot : launch) {
             const topk_status rs = dispatch(s, *slot);
+            const uint64_t held = slot_held(*slot); // a larger request may have grown the slot's scratch
+            if (held != slot->held) {
+                std::lock_guard<std::mutex> lock(s->mu);
+                s->st.reserved_bytes += held - slot->held;
+                slot->held = held;
+            }
             if (rs != TOPK_OK) { // nothing (more) will complete on this slot's event: retire now
                 cudaStreamSynchronize(slot->stream);
                 cudaGetLastError();
@@ -248,6 +271,10 @@ topk_status topk_serve_create(topk_server** out, int device, uint64_t hbm_budget
     if (rs != TOPK_OK) {
         topk_serve_destroy(s);
         return rs;
+    }
+    for (Slot& slot : s->slots) {
+        slot.held = slot_held(slot);
+        s->st.reserved_bytes += slot.held;
     }
     s->worker = std::thread(worker_main, s);
     *out = s;

@@ -73,7 +73,7 @@ def test_struct_layouts_match_binding(tmp_path):
                    " offsetof(topk_params, block_threads));\n"
                    '  printf("%zu %zu\\n", sizeof(topk_stats), offsetof(topk_stats, sample_kept));\n'
                    '  printf("%zu %zu\\n", sizeof(topk_request), offsetof(topk_request, arrival_ns));\n'
-                   '  printf("%zu %zu\\n", sizeof(topk_serve_report), offsetof(topk_serve_report, elapsed_s));\n'
+                   '  printf("%zu %zu\\n", sizeof(topk_serve_report), offsetof(topk_serve_report, budget_waits));\n'
                    '  printf("%zu %zu %zu\\n", sizeof(topk_freq_params), offsetof(topk_freq_params, seed),'
                    " offsetof(topk_freq_params, max_distinct));\n"
                    "  return 0;\n}\n")
@@ -84,7 +84,7 @@ def test_struct_layouts_match_binding(tmp_path):
     assert got[0] == [ctypes.sizeof(tk.topk_params), tk.topk_params.flags.offset, tk.topk_params.block_threads.offset]
     assert got[1] == [ctypes.sizeof(tk.topk_stats), tk.topk_stats.sample_kept.offset]
     assert got[2] == [ctypes.sizeof(tk.topk_request), tk.topk_request.arrival_ns.offset]
-    assert got[3] == [ctypes.sizeof(tk.topk_serve_report), tk.topk_serve_report.elapsed_s.offset]
+    assert got[3] == [ctypes.sizeof(tk.topk_serve_report), tk.topk_serve_report.budget_waits.offset]
     assert got[4] == [ctypes.sizeof(tk.topk_freq_params), tk.topk_freq_params.seed.offset,
                       tk.topk_freq_params.max_distinct.offset]
 

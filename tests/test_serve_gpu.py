@@ -125,6 +125,10 @@ def test_serve_budget(tk):
         assert same_result(outs[i], tk.topk_select(ctx, keys, 10 + i))
     st = srv.stats()
     assert st["peak_inflight_bytes"] <= need + (1 << 16)
+    # the slots' own device memory is reported beside the budget: at least the
+    # scratch each of the 4 slots reserves for a 2^26-key selection
+    assert st["reserved_bytes"] >= 4 * (1 << 26) // 16
+    assert st["budget_waits"] >= 1  # six requests, room for one at a time
     srv.close()
     ctx.close()
 

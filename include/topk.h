@@ -387,13 +387,12 @@ topk_status topk_tuning_load(topk_ctx *ctx, const char *path);
  *              the caller at all (the outputs are then undefined).
  * The first call on a device does a one-time set-up there: it looks up the
  * array's device address (cudaGetSymbolAddress) and sets the kernel
- * attributes and launch geometry of all five key types.  Make that first
- * call before any stream capture.  The call itself calls no cudaMalloc,
- * cudaFree or other allocating routine.  All calls in the process share the
- * one array per device, which keeps the contents left by the last call (each
- * call clears what must start at zero): calls whose work may overlap on the
- * GPU (different streams, or threads) race and must be serialised by the
- * caller. */
+ * attributes and launch geometry of all five key types.  The call itself
+ * calls no cudaMalloc, cudaFree or other allocating routine.  All calls in
+ * the process share the one array per device, which keeps the contents left
+ * by the last call (each call clears what must start at zero): calls whose
+ * work may overlap on the GPU (different streams, or threads) race and must
+ * be serialised by the caller. */
 topk_status topk_select_noalloc(const void *d_keys, uint64_t n, uint64_t k,
                                 topk_dtype dtype, void *d_out_keys, uint32_t *d_out_idx,
                                 void *d_kth_key, uint32_t *d_kth_idx, uint32_t *d_status,

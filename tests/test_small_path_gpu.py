@@ -1,0 +1,164 @@
+"""The one-launch path of topk_select (GPU): inputs of up to 2^22 keys whose
+first bracket fits the finishing block are selected by one cooperative
+kernel (sample, pivots, pass, grid barrier, in-block finish).
+
+Each case checks that the path was taken (one kernel launch, counted by the
+context's measurement hooks) and that the result is the oracle's, bit for
+bit; the boundary cases check that the grid path takes over above 2^22 keys
+and for brackets too wide for the finishing block.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1502_03942_gb300 import workloads as wl
+
+from _gpu import bits_of, check_against_oracle, to_device
+
+pytestmark = pytest.mark.gpu
+
+SMALL_MAX = 1 << 22
+
+
+@pytest.fixture(scope="module")
+def tk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1502_03942_gb300 as tk
+    return tk
+
+
+@pytest.fixture(scope="module")
+def ctx(tk):
+    c = tk.Context(0)
+    c.profile(True)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    return oracle.default()
+
+
+def keys_for(name, n, seed):
+    g = np.random.Generator(np.random.Philox(seed))
+    if name in ("u32", "i32"):
+        return wl.uniform_u32(n, seed)
+    if name == "f32":
+        return wl.normal_f32(n, seed).view(np.uint32)
+    if name == "bf16":
+        return g.integers(0, 1 << 16, size=n, dtype=np.uint32).astype(np.uint16)
+    return wl.uniform_u64(n, seed)
+
+
+def launches_of(ctx, run):
+    ctx.profile_read(reset=True)
+    out = run()
+    return out, ctx.profile_read(reset=True)["launches"]
+
+
+# (key type, n, k): brackets of a few thousand keys at most (64-bit keys have
+# half the finishing block's room, so smaller k), sizes from just above the
+# one-block range to the path's limit, ragged and power-of-two
+CASES = [
+    ("u32", 16385, 2),
+    ("u32", 1 << 20, 1000),
+    ("u32", SMALL_MAX, 4000),
+    ("i32", 300007, 777),
+    ("f32", (1 << 21) + 3, 100),
+    ("f32", SMALL_MAX, 3000),
+    ("bf16", SMALL_MAX, 5000),
+    ("bf16", 999_999, 2),
+    ("u64", 1_000_003, 50),
+    ("u64", SMALL_MAX, 100),
+]
+
+
+@pytest.mark.parametrize("name,n,k", CASES)
+def test_one_launch_exact(tk, ctx, orc, name, n, k):
+    keys = keys_for(name, n, seed=n % 9973 + k)
+    d = to_device(keys, name)
+    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k))
+    assert launches == 1, "expected the one-launch path"
+    check_against_oracle(keys, name, k, out, orc)
+    # a second call on the same context (grid-barrier words reused)
+    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k))
+    assert launches == 1
+    check_against_oracle(keys, name, k, out, orc)
+
+
+def test_grid_path_above_the_limit(tk, ctx, orc):
+    """One key more than the limit, or a bracket wider than the finishing
+    block, takes the grid levels (more than one launch), with the same
+    result rules."""
+    n = SMALL_MAX + 1
+    keys = keys_for("u32", n, seed=5)
+    d = to_device(keys, "u32")
+    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, 100))
+    assert launches > 1
+    check_against_oracle(keys, "u32", 100, out, orc)
+    n = 1 << 20
+    keys = keys_for("u32", n, seed=6)
+    d = to_device(keys, "u32")
+    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, n // 2))
+    assert launches > 1
+    check_against_oracle(keys, "u32", n // 2, out, orc)
+
+
+def test_one_launch_forced_pivot_failures(tk, ctx, orc):
+    """A margin far too narrow (z = 0.25, used as given) misses rank k in the
+    one-launch kernel's level; the in-block levels that follow must still
+    find the exact set."""
+    n = SMALL_MAX
+    keys = keys_for("u32", n, seed=7)
+    d = to_device(keys, "u32")
+    failures = 0
+    for k in (17, 900, 3000):
+        p = tk.make_params(delta_factor=0.25, flags=tk.TOPK_FLAG_RAW_DELTA)
+        out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k, params=p))
+        assert launches == 1
+        check_against_oracle(keys, "u32", k, out, orc)
+        failures += ctx.last_stats()["pivot_failures"]
+    assert failures > 0, "the narrow margin should have missed rank k at least once"
+
+
+@pytest.mark.parametrize("name", ["f32", "u64"])
+def test_one_launch_largest_and_kth(tk, ctx, orc, name):
+    n = 1 << 21
+    k = 64
+    keys = keys_for(name, n, seed=8)
+    d = to_device(keys, name)
+    p = tk.make_params(flags=tk.TOPK_FLAG_LARGEST)
+    (ok, oi, kk, ki), launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k, params=p))
+    assert launches == 1
+    want_sel, want_kth = orc.select_largest(keys, name, k)
+    got = bits_of(oi)
+    assert np.array_equal(np.sort(got), np.sort(want_sel))
+    assert np.array_equal(bits_of(ok), keys[got])
+    assert int(bits_of(ki)[0]) == want_kth and int(bits_of(kk)[0]) == int(keys[want_kth])
+    (kk, ki), launches = launches_of(ctx, lambda: tk.topk_select_kth(ctx, d, k))
+    assert launches == 1
+    _, want = orc.select(keys, name, k)
+    assert int(bits_of(ki)[0]) == want and int(bits_of(kk)[0]) == int(keys[want])
+
+
+def test_one_launch_unaligned_and_ties(tk, ctx, orc):
+    """An input that starts 4 bytes past a 16-byte boundary, and one of seven
+    distinct values (ties split by position)."""
+    n = (1 << 20) + 1
+    keys = keys_for("f32", n, seed=9)
+    d = to_device(keys, "f32")
+    sub = d[1:]
+    assert sub.data_ptr() % 16 == 4
+    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, sub, 500))
+    assert launches == 1
+    check_against_oracle(keys[1:].copy(), "f32", 500, out, orc)
+    g = np.random.Generator(np.random.Philox(10))
+    ties = (np.array([0.0, -0.0, 1.0, -1.0, 2.5, np.inf, -np.inf], np.float32)[g.integers(0, 7, size=n)]
+            ).view(np.uint32)
+    d = to_device(ties, "f32")
+    for k in (2, 1000):
+        out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k))
+        assert launches == 1
+        check_against_oracle(ties, "f32", k, out, orc)

@@ -184,6 +184,13 @@ struct alignas(16) SelState {
     u32 dense;            // the armed pass expects many a-elements
 };
 
+// Number of significant bits of v (0 for 0).
+__device__ __forceinline__ int bit_length_fast(u64 v) { return v ? 64 - __clzll((long long)v) : 0; }
+__device__ __forceinline__ int bit_length_fast(u128 v) {
+    const u64 hi = (u64)(v >> 64);
+    return hi ? 128 - __clzll((long long)hi) : bit_length_fast((u64)v);
+}
+
 // Arguments common to every kernel of one topk_select call.
 struct SelArgs {
     const void* keys;         // input (raw keys)
@@ -208,10 +215,18 @@ struct SelArgs {
     // grid-level sampling (k_sample / k_pivots) and the end-of-pass branch
     void* samp;               // sample composites, capacity samp_cap
     u32* samp_count;          // number drawn into samp (zero between levels)
-    u32* hist;                // HIST_BINS bins over the window (zero between levels)
     u32* pass_done;           // block-done counter of the pass (zero between passes)
     u32 samp_cap;
     u32* gbar;                // one-launch path: grid barrier words (arrivals, generation)
+    int first_dense;          // first level's pass mode chosen by the host (0/1), or -1
+};
+
+// Words of the cooperative launch of one call (SelArgs::gbar), all zero when
+// the call starts.
+struct CoopWords {
+    u32 bar[2];             // [0] grid-barrier arrival count, [1] unused
+    u32 scnt[2];            // sample sizes, by level parity
+    u64 cnt_a[2], cnt_b[2]; // pass counters, by level parity
 };
 
 // Largest composite of a key type's domain (the first window's upper end):
@@ -223,24 +238,6 @@ template <int DT> __host__ __device__ inline u128 key_domain_max() {
                        : (((u128)(B == DT_BF16 ? 0xFFFFu : 0xFFFFFFFFu)) << 32) | 0xFFFFFFFFu;
 }
 
-// Histogram of a window [lo, hi]: bin = (c - lo) >> sh with the shift chosen
-// so that every composite of the window falls in one of HIST_BINS bins.
-constexpr u32 HIST_BITS = 12;
-constexpr u32 HIST_BINS = 1u << HIST_BITS;
-
-__device__ __forceinline__ int bit_length_fast(u64 v) { return v ? 64 - __clzll((long long)v) : 0; }
-__device__ __forceinline__ int bit_length_fast(u128 v) {
-    const u64 hi = (u64)(v >> 64);
-    return hi ? 128 - __clzll((long long)hi) : bit_length_fast((u64)v);
-}
-template <class CT> __device__ __forceinline__ u32 hist_shift(CT lo, CT hi) {
-    const int b = bit_length_fast((CT)(hi - lo));
-    return b > (int)HIST_BITS ? (u32)(b - HIST_BITS) : 0u;
-}
-template <class CT> __device__ __forceinline__ u32 hist_bin(CT c, CT lo, u32 sh) {
-    const CT d = (CT)(c - lo) >> sh;
-    return d < (CT)HIST_BINS ? (u32)d : HIST_BINS - 1;
-}
 
 // ------------------------------------------------- dependent launches
 // The kernels of one call are launched with programmatic stream

@@ -122,11 +122,11 @@ topk_status topk_ctx_create(topk_ctx** out, int device) {
         cudaDeviceProp prop;
         if (cudaGetDeviceProperties(&prop, device) == cudaSuccess) c->device_name = prop.name;
     }
-    // error word, block-done counters (64 slots), the state and the sample
-    // histogram: one allocation, zeroed once; every kernel that uses a
-    // counter or the histogram leaves it at zero
+    // error word, block-done counters (64 slots) and the state: one
+    // allocation, zeroed once; every kernel that uses a counter leaves it at
+    // zero
     void* p = nullptr;
-    const size_t bytes = 256 + 64 * sizeof(u32) + 4096 + HIST_BINS * sizeof(u32);
+    const size_t bytes = 256 + 64 * sizeof(u32) + 4096;
     if (cudaMalloc(&p, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -136,7 +136,6 @@ topk_status topk_ctx_create(topk_ctx** out, int device) {
     c->d_err = static_cast<u32*>(p);
     c->d_counter = reinterpret_cast<u32*>(static_cast<char*>(p) + 256);
     c->d_state = static_cast<char*>(p) + 256 + 64 * sizeof(u32);
-    c->d_hist = reinterpret_cast<u32*>(static_cast<char*>(p) + 256 + 64 * sizeof(u32) + 4096);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         cudaFree(p);
         delete c;

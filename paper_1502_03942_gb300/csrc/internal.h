@@ -41,7 +41,6 @@ struct topk_ctx {
     uint32_t* d_err = nullptr;     // first device error (latched), own allocation
     uint32_t* d_counter = nullptr; // last-block-done counters (zero between calls)
     void* d_state = nullptr;       // selection state (SelState or RunsState)
-    uint32_t* d_hist = nullptr;    // sample histogram (zero between levels)
     int last_kind = topk::LAST_NONE;
     // small selections may run as one cooperative launch (off for contexts
     // whose work shares the GPU with concurrent kernels: the serving slots)

@@ -93,8 +93,12 @@ template <int DT> __device__ void init_state(SelState* g, const SelArgs& a) { *g
 
 // ------------------------------------------------------------ one pass
 
+// One pass over the source of state `s` (tiles tile0, tile0 + step, ...):
+// a to the output, b to candidate buffer s.dst, the counts reserved on
+// *cnt_a and *cnt_b.
 template <int NT, int DT, bool INPUT_ONLY = false, bool ONLY_EXACT = false>
-__device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 step, PassSmem<NT>& ps) {
+__device__ void run_pass_to(const SelArgs& a, const SelState& s, u64 tile0, u64 step, PassSmem<NT>& ps, u64* cnt_a,
+                            u64* cnt_b) {
     typedef Key<DT> K;
     typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
@@ -109,8 +113,8 @@ __device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 ste
     sink.ck = static_cast<key_t*>(a.cand_key[s.dst - 1]);
     sink.ci = a.cand_idx[s.dst - 1];
     sink.cap_b = a.cap_b;
-    sink.cnt_a = &a.st->cnt_a;
-    sink.cnt_b = &a.st->cnt_b;
+    sink.cnt_a = cnt_a;
+    sink.cnt_b = cnt_b;
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
     const bool has_a = pl > lo, exact = ONLY_EXACT || lo != (ct)0;
     if (INPUT_ONLY || s.src == SRC_INPUT) {
@@ -128,6 +132,12 @@ __device__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 ste
             else pass_tiles<NT, false, false, DT>(src, tile0, step, lo, pl, pr, sink, ps);
         }
     }
+}
+
+template <int NT, int DT, bool INPUT_ONLY = false, bool ONLY_EXACT = false>
+__device__ __forceinline__ void run_pass(const SelArgs& a, const SelState& s, u64 tile0, u64 step,
+                                         PassSmem<NT>& ps) {
+    run_pass_to<NT, DT, INPUT_ONLY, ONLY_EXACT>(a, s, tile0, step, ps, &a.st->cnt_a, &a.st->cnt_b);
 }
 
 // ------------------------------------------------------- pickPivots
@@ -171,8 +181,10 @@ template <int DT, class SM> __device__ void plan_level(const SelArgs& a, SM& sm,
             const long long jl = sm.jl, jr = sm.jr;
             const long long top = (long long)kept - 1;
             const u32 r0 = (u32)(jl < 0 ? 0 : jl > top ? top : jl), r1 = (u32)(jr < 0 ? 0 : jr > top ? top : jr);
-            if (jl >= 0) pl = block_select_hist<KW, SM::THREADS>(sm.samp, kept, lo, hi, r0, sm.hs);
-            if (jr <= top) pr = block_select_hist<KW, SM::THREADS>(sm.samp, kept, lo, hi, r1, sm.hs);
+            ct x0, x1;
+            block_select_two<KW, SM::THREADS>(sm.samp, kept, lo, hi, r0, r1, sm.hs, x0, x1);
+            if (jl >= 0) pl = x0;
+            if (jr <= top) pr = x1;
         }
     }
     if (threadIdx.x == 0) {

@@ -965,7 +965,7 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
     for (int o = 16; o > 0; o >>= 1) {
         const u64 lo64 = __shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)x, o);
         ct y = (ct)lo64;
-        if (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
+        if constexpr (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
         x |= y;
     }
     if (lane == 0) sm.diff[warp] = x;
@@ -978,8 +978,8 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
     ct top = 0; // mask of the shared leading digits
     if (d0 > 0) {
         const int keep = 8 * (C::DIGITS - (d0 < C::DIGITS ? d0 : C::DIGITS));
-        top = (keep >= TOTAL) ? (ct)0 : (ct)(((ct)1 << TOTAL) - 1) & ~(ct)(((ct)1 << keep) - 1);
-        if (TOTAL == 64) top = keep >= 64 ? (ct)0 : (ct)(~(u64)0 << keep);
+        if constexpr (TOTAL == 64) top = keep >= 64 ? (ct)0 : (ct)(~(u64)0 << keep);
+        else top = (keep >= TOTAL) ? (ct)0 : (ct)(((ct)1 << TOTAL) - 1) & ~(ct)(((ct)1 << keep) - 1);
     }
     if (tid < NTGT) {
         sm.prefix[tid] = count > 0 ? (v[0] & top) : (ct)0;
@@ -1085,13 +1085,50 @@ __device__ void block_select_ranks(const typename Comp<KW>::t* v, u32 count, con
     __syncthreads();
 }
 
+// A composite from lane `src` (all 32 lanes call).
+template <class CT> __device__ __forceinline__ CT shfl_comp(CT x, u32 src) {
+    CT y = (CT)__shfl_sync(0xffffffffu, (unsigned long long)(u64)x, src);
+    if constexpr (sizeof(CT) > 8)
+        y |= (CT)__shfl_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), src) << 64;
+    return y;
+}
+
+// Selection among at most 64 elements by counting (one warp, no shared
+// memory): lane l holds v[l] and v[l + 32]; an element's place in the sorted
+// order, ties by index, is the number of smaller elements plus the number of
+// equal ones before it, and exactly one element has place `rank`.
+template <int KW>
+__device__ typename Comp<KW>::t warp_rank_small(const typename Comp<KW>::t* v, u32 count, u32 rank) {
+    typedef typename Comp<KW>::t ct;
+    const u32 lane = lane_id();
+    const bool h0 = lane < count, h1 = lane + 32 < count;
+    const ct e0 = h0 ? v[lane] : (ct)0, e1 = h1 ? v[lane + 32] : (ct)0;
+    u32 p0 = 0, p1 = 0;
+    const u32 n0 = count < 32 ? count : 32;
+    for (u32 j = 0; j < n0; ++j) { // element j (index j < 32)
+        const ct o = shfl_comp(e0, j);
+        p0 += (u32)(o < e0 || (o == e0 && j < lane));
+        p1 += (u32)(o <= e1); // index j < lane + 32
+    }
+    for (u32 j = 0; j + 32 < count; ++j) { // element 32 + j
+        const ct o = shfl_comp(e1, j);
+        p0 += (u32)(o < e0); // index 32 + j > lane
+        p1 += (u32)(o < e1 || (o == e1 && j < lane));
+    }
+    const u32 m0 = __ballot_sync(0xffffffffu, h0 && p0 == rank);
+    const u32 m1 = __ballot_sync(0xffffffffu, h1 && p1 == rank);
+    return m0 ? shfl_comp(e0, (u32)__ffs(m0) - 1) : shfl_comp(e1, (u32)__ffs(m1) - 1);
+}
+
 // Warp-level version for small sets: one warp selects the element of 0-based
 // rank `rank` among v[0..count) with its own 256-bin histogram in shared
-// memory (no block barrier, so several warps can select concurrently).
+// memory (no block barrier, so several warps can select concurrently); up to
+// 64 elements by counting instead.
 template <int KW>
 __device__ typename Comp<KW>::t warp_select_rank(const typename Comp<KW>::t* v, u32 count, u32 rank, u32* hist) {
     typedef Comp<KW> C;
     typedef typename C::t ct;
+    if (count <= 64) return warp_rank_small<KW>(v, count, rank);
     const u32 lane = lane_id();
     const ct v0 = v[0];
     ct x = 0;
@@ -1099,7 +1136,7 @@ __device__ typename Comp<KW>::t warp_select_rank(const typename Comp<KW>::t* v, 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         ct y = (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)x, o);
-        if (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
+        if constexpr (sizeof(ct) > 8) y |= (ct)__shfl_xor_sync(0xffffffffu, (unsigned long long)(u64)((u128)x >> 64), o) << 64;
         x |= y;
     }
     if (x == 0) return v0; // all equal
@@ -1175,7 +1212,7 @@ __device__ typename Comp<KW>::t warp_select_rank(const typename Comp<KW>::t* v, 
             const u32 who = __ffs(__ballot_sync(0xffffffffu, found)) - 1;
             const u64 lo64 = __shfl_sync(0xffffffffu, (unsigned long long)(u64)res, who);
             ct out = (ct)lo64;
-            if (sizeof(ct) > 8) out |= (ct)__shfl_sync(0xffffffffu, (unsigned long long)(u64)((u128)res >> 64), who) << 64;
+            if constexpr (sizeof(ct) > 8) out |= (ct)__shfl_sync(0xffffffffu, (unsigned long long)(u64)((u128)res >> 64), who) << 64;
             return out;
         }
     }
@@ -1201,10 +1238,11 @@ template <int KW> struct HistSelSmem {
     typedef typename Comp<KW>::t ct;
     u32 hist[HS_BINS];
     ct gath[HS_GATHER];
-    u32 whist[256];
+    u32 whist[2][256];
     u32 wsum[32];
-    ct wlo, whi, result;
+    ct wlo, whi, result, res2[2];
     u32 rank, bin, below, cnt, ng;
+    u32 bin2[2], below2[2], cnt2[2], ng2[2];
 };
 
 template <int KW, int NT>
@@ -1276,24 +1314,18 @@ __device__ typename Comp<KW>::t block_select_hist(const typename Comp<KW>::t* v,
         __syncthreads();
         const u32 b = hs.bin, cnt = hs.cnt, rr = r - hs.below;
         if (cnt <= HS_GATHER) {
-            // the bin's elements, then one warp ranks them
-            for (u32 i0 = 0; i0 < count; i0 += NT) {
-                const u32 i = i0 + tid;
-                ct c = 0;
-                bool in = false;
-                if (i < count) {
-                    c = v[i];
-                    in = c >= wlo && c <= whi && bin_of(c) == b;
+            // the bin's elements (few: each takes its own slot), then one
+            // warp ranks them
+            for (u32 i = tid; i < count; i += NT) {
+                const ct c = v[i];
+                if (c >= wlo && c <= whi && bin_of(c) == b) {
+                    const u32 slot = atomicAdd(&hs.ng, 1u);
+                    if (slot < HS_GATHER) hs.gath[slot] = c;
                 }
-                const u32 bal = __ballot_sync(0xffffffffu, in);
-                u32 base = 0;
-                if (lane == 0 && bal) base = atomicAdd(&hs.ng, (u32)__popc(bal));
-                base = __shfl_sync(0xffffffffu, base, 0) + (u32)__popc(bal & lanemask_lt());
-                if (in && base < HS_GATHER) hs.gath[base] = c;
             }
             __syncthreads();
             if (warp == 0) {
-                const ct res = warp_select_rank<KW>(hs.gath, cnt, rr, hs.whist);
+                const ct res = warp_select_rank<KW>(hs.gath, cnt, rr, hs.whist[0]);
                 if (lane == 0) hs.result = res;
             }
             __syncthreads();
@@ -1302,14 +1334,127 @@ __device__ typename Comp<KW>::t block_select_hist(const typename Comp<KW>::t* v,
         // a large bin: narrow the window to it and repeat
         if (tid == 0) {
             const ct nlo = (ct)(wlo + ((ct)b << sh));
-            const ct top = (ct)(nlo + (((ct)1 << sh) - 1));
+            const ct top = (ct)(nlo + (((ct)1 << sh) - 1)); // wraps past the largest composite
             hs.wlo = nlo;
-            hs.whi = (b == HS_BINS - 1 || top > whi) ? whi : top;
+            hs.whi = (b == HS_BINS - 1 || top > whi || top < nlo) ? whi : top;
             hs.rank = rr;
         }
         __syncthreads();
     }
     return hs.wlo; // not reached: each step narrows the window by 2^HS_BITS
+}
+
+// The elements of ranks r0 and r1 among v[0..count) (all in [lo, hi]) at
+// once: one histogram pass finds both bins, one gather pass collects both,
+// and two warps rank them concurrently.  A bin too large to gather is
+// selected by block_select_hist on that bin's window alone.
+template <int KW, int NT>
+__device__ void block_select_two(const typename Comp<KW>::t* v, u32 count, typename Comp<KW>::t lo,
+                                 typename Comp<KW>::t hi, u32 r0, u32 r1, HistSelSmem<KW>& hs,
+                                 typename Comp<KW>::t& out0, typename Comp<KW>::t& out1) {
+    typedef typename Comp<KW>::t ct;
+    static_assert(HS_BINS % NT == 0 && NT <= 1024 && NT >= 64, "bins per thread");
+    constexpr u32 PER = HS_BINS / NT;
+    constexpr u32 HALF = HS_GATHER / 2;
+    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    const int bl = bit_length_fast((ct)(hi - lo));
+    const u32 sh = bl > (int)HS_BITS ? (u32)(bl - HS_BITS) : 0u;
+    auto bin_of = [&](ct c) -> u32 {
+        const ct d = (ct)(c - lo) >> sh;
+        return d < (ct)HS_BINS ? (u32)d : HS_BINS - 1;
+    };
+    for (u32 i = tid; i < HS_BINS; i += NT) hs.hist[i] = 0;
+    __syncthreads();
+    for (u32 i = tid; i < count; i += NT) {
+        const ct c = v[i];
+        if (c >= lo && c <= hi) atomicAdd(&hs.hist[bin_of(c)], 1u);
+    }
+    __syncthreads();
+    u32 h[PER], t = 0;
+#pragma unroll
+    for (u32 q = 0; q < PER; ++q) {
+        h[q] = hs.hist[tid * PER + q];
+        t += h[q];
+    }
+    u32 incl = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (u32)o) incl += y;
+    }
+    if (lane == 31) hs.wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const u32 x = lane < NT / 32 ? hs.wsum[lane] : 0u;
+        u32 wi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= (u32)o) wi += y;
+        }
+        if (lane < NT / 32) hs.wsum[lane] = wi - x;
+    }
+    __syncthreads();
+    u32 run = hs.wsum[warp] + incl - t;
+#pragma unroll
+    for (u32 q = 0; q < PER; ++q) {
+        if (h[q] && r0 >= run && r0 < run + h[q]) {
+            hs.bin2[0] = tid * PER + q;
+            hs.below2[0] = run;
+            hs.cnt2[0] = h[q];
+        }
+        if (h[q] && r1 >= run && r1 < run + h[q]) {
+            hs.bin2[1] = tid * PER + q;
+            hs.below2[1] = run;
+            hs.cnt2[1] = h[q];
+        }
+        run += h[q];
+    }
+    if (tid == 0) hs.ng2[0] = hs.ng2[1] = 0;
+    __syncthreads();
+    const u32 b0 = hs.bin2[0], b1 = hs.bin2[1], c0 = hs.cnt2[0], c1 = hs.cnt2[1];
+    const bool same = b0 == b1;
+    if (same ? c0 <= HS_GATHER : (c0 <= HALF && c1 <= HALF)) {
+        const u32 off1 = same ? 0u : HALF;
+        const u32 cap0 = same ? HS_GATHER : HALF;
+        // the two bins' elements (few: each takes its own slot)
+        for (u32 i = tid; i < count; i += NT) {
+            const ct c = v[i];
+            if (c >= lo && c <= hi) {
+                const u32 b = bin_of(c);
+                if (b == b0) {
+                    const u32 slot = atomicAdd(&hs.ng2[0], 1u);
+                    if (slot < cap0) hs.gath[slot] = c;
+                } else if (b == b1) {
+                    const u32 slot = atomicAdd(&hs.ng2[1], 1u);
+                    if (slot < HALF) hs.gath[off1 + slot] = c;
+                }
+            }
+        }
+        __syncthreads();
+        if (warp < 2) {
+            const ct res = warp == 0 ? warp_select_rank<KW>(hs.gath, c0, r0 - hs.below2[0], hs.whist[0])
+                                     : warp_select_rank<KW>(hs.gath + off1, c1, r1 - hs.below2[1], hs.whist[1]);
+            if (lane == 0) hs.res2[warp] = res;
+        }
+        __syncthreads();
+        out0 = hs.res2[0];
+        out1 = hs.res2[1];
+        return;
+    }
+    // a large bin: select inside its own window
+    const u32 bb[2] = {b0, b1}, rr[2] = {r0 - hs.below2[0], r1 - hs.below2[1]};
+    ct res[2];
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+        const ct nlo = (ct)(lo + ((ct)bb[q] << sh));
+        const ct top = (ct)(nlo + (((ct)1 << sh) - 1));
+        const ct nhi = (bb[q] == HS_BINS - 1 || top > hi || top < nlo) ? hi : top;
+        __syncthreads(); // every thread has read the bins above before hs is reused
+        res[q] = block_select_hist<KW, NT>(v, count, nlo, nhi, rr[q], hs);
+    }
+    out0 = res[0];
+    out1 = res[1];
 }
 
 // ------------------------------------------------------------- sampling

@@ -50,330 +50,12 @@ __device__ __forceinline__ void pass_epilogue(const SelArgs& a) {
     }
 }
 
-// ---- pickPivots, part 1: the sample (whole grid)
-// Every thread makes SMP_DRAWS per-partition draws of the current window,
-// appends the kept ones to the sample array and counts them in a shared
-// histogram over the window, added to the global histogram at the end.
+// ---- pickPivots: the sample (k_sample, whole grid) and the pivots
+// (k_pivots, one block), defined with the sampling routines further down.
 constexpr int SMP_NT = 128;
 constexpr int SMP_DRAWS = 4;        // one Philox block per thread
 constexpr u32 SMP_MAX_SCALE = 4;    // extra draws for a narrowed window
-
-template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, int first) {
-    grid_dep_wait();
-    grid_dep_release();
-    typedef Key<DT> K;
-    typedef typename K::key_t key_t;
-    constexpr int KW = K::KW;
-    typedef Comp<KW> C;
-    typedef typename C::t ct;
-    __shared__ u32 hist[HIST_BINS];
-    for (u32 i = threadIdx.x; i < HIST_BINS; i += blockDim.x) hist[i] = 0;
-    SelState s;
-    if (first) {
-        s.lo = 0;
-        s.hi = key_domain_max<DT>();
-        s.m_src = a.n;
-        s.m_win = a.n;
-        s.src = SRC_INPUT;
-        s.level = 0;
-        s.phase = PH_RUN;
-    } else {
-        s = *a.st;
-    }
-    __syncthreads();
-    if (s.phase != PH_RUN || s.m_src <= a.grid_G || s.m_win <= a.finish_T) return;
-    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
-    const u32 sh = hist_shift(lo, hi);
-    u32 draws = a.sample;
-    if (s.m_win < s.m_src) { // narrowed window: draw more so that enough land inside
-        u64 ratio = s.m_src / (s.m_win ? s.m_win : 1);
-        ratio = ratio < 1 ? 1 : ratio > SMP_MAX_SCALE ? SMP_MAX_SCALE : ratio;
-        draws = (u32)((u64)draws * ratio);
-    }
-    if (blockIdx.x * SMP_NT * SMP_DRAWS >= draws) return; // the whole block draws nothing
-    const u32 m = (u32)s.m_src; // sources hold fewer than 2^32 elements
-    const u32 p = a.parts < m ? a.parts : m;
-    const u32 len = m / p, rem = m - len * p;
-    const u32 j0 = (blockIdx.x * SMP_NT + threadIdx.x) * SMP_DRAWS;
-    const Philox4 r = philox4x32_10(j0, s.level, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
-    key_t kk[SMP_DRAWS];
-    u32 ii[SMP_DRAWS];
-    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, m);
-    const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
-                           a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], m};
-    u32 keepm = 0; // bit q: draw q is inside the window
-#pragma unroll
-    for (int q = 0; q < SMP_DRAWS; ++q) {
-        const u32 j = j0 + q;
-        const u32 part = j % p; // draws dealt round-robin: an equal share per partition
-        const u32 plo = part * len + (part < rem ? part : rem);
-        const u32 psz = len + (part < rem ? 1 : 0);
-        const u32 pos = plo + (u32)(((u64)r.v[q] * psz) >> 32);
-        kk[q] = 0;
-        ii[q] = 0;
-        if (j < draws) {
-            if (s.src == SRC_INPUT) isrc.at(pos, kk[q], ii[q]);
-            else csrc.at(pos, kk[q], ii[q]);
-            const ct c = C::make(kk[q], ii[q]);
-            if (c >= lo && c <= hi) keepm |= 1u << q;
-        }
-    }
-    // one slot reservation per warp for all its kept draws
-    const u32 cnt = (u32)__popc(keepm);
-    u32 incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane_id() >= (u32)o) incl += y;
-    }
-    const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
-    u32 slot0 = 0;
-    if (lane_id() == 31 && tot) slot0 = atomicAdd(a.samp_count, tot);
-    u32 slot = __shfl_sync(0xffffffffu, slot0, 31) + incl - cnt;
-    ct* samp = static_cast<ct*>(a.samp);
-#pragma unroll
-    for (int q = 0; q < SMP_DRAWS; ++q) {
-        if ((keepm >> q) & 1u) {
-            const ct c = C::make(kk[q], ii[q]);
-            if (slot < a.samp_cap) {
-                samp[slot] = c;
-                atomicAdd(&hist[hist_bin(c, lo, sh)], 1u);
-            } else {
-                keepm &= ~(1u << q);
-            }
-            ++slot;
-        }
-    }
-    __syncthreads();
-    // each touched bin is moved to the global histogram once (the first
-    // thread to take it)
-#pragma unroll
-    for (int q = 0; q < SMP_DRAWS; ++q) {
-        if (!((keepm >> q) & 1u)) continue;
-        const u32 b = hist_bin(C::make(kk[q], ii[q]), lo, sh);
-        const u32 v = atomicExch(&hist[b], 0u);
-        if (v) atomicAdd(a.hist + b, v);
-    }
-}
-
-// ---- pickPivots, part 2 (one block): pivots from the histogram and the
-// sample.  The bins holding sample ranks k|S|/n -/+ Delta are found from the
-// histogram's prefix sums; only the sample elements of those bins are
-// gathered and ranked exactly.  Leaves the histogram and the sample count at
-// zero for the next level.
 constexpr int PIV_NT = 1024;
-
-template <int KW> struct PivotSmem {
-    typedef typename Comp<KW>::t ct;
-    ct buf[Lim<KW>::ELEMS];
-    u32 warp_sum[PIV_NT / 32];
-    RadixSmem<KW, 2> rs2;
-    RadixSmem<KW, 1> rs1;
-    u32 bin[2], base[2], cnt[2], want[2];
-    u32 flag, collect, kept;
-    long long jl, jr;
-    u32 whist[2][256];
-    ct wres[2];
-};
-
-constexpr u32 WARP_SELECT_MAX = 512; // bins up to this size are ranked by one warp, larger ones by the block
-
-template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, int first) {
-    grid_dep_wait();
-    grid_dep_release();
-    constexpr int KW = Key<DT>::KW;
-    typedef Comp<KW> C;
-    typedef typename C::t ct;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<PivotSmem<KW>*>(smem_raw);
-    SelState* g = a.st;
-    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
-    // the histogram and the state are loaded at once (independent round trips)
-    u32 h[4], t = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) h[q] = a.hist[tid * 4 + q];
-    const SelState s = first ? initial_state<DT>(a) : *g;
-    if (tid == 0) {
-        if (first) *g = s;
-        u32 go = s.phase == PH_RUN;
-        if (go && s.m_src <= a.grid_G) {
-            g->phase = PH_FINISH;
-            go = 0;
-        }
-        sm.flag = go;
-        sm.collect = s.m_win <= a.finish_T;
-        const u32 c = *a.samp_count;
-        sm.kept = c < a.samp_cap ? c : a.samp_cap;
-        // pivot ranks once (the block shares them)
-        long long jl = -1, jr = 0;
-        if (go && sm.kept > 0)
-            pivot_ranks(sm.kept, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
-        sm.jl = jl;
-        sm.jr = jr;
-        for (int q = 0; q < 2; ++q) {
-            sm.bin[q] = 0xFFFFFFFFu;
-            sm.base[q] = 0;
-            sm.cnt[q] = 0;
-        }
-    }
-    __syncthreads();
-    if (sm.flag) {
-        const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
-        ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
-        const u32 kept = sm.kept;
-        const long long jl = sm.jl, jr = sm.jr;
-        if (!sm.collect && kept > 0) {
-            const long long top = (long long)kept - 1;
-            const u32 rl = (u32)(jl < 0 ? 0 : jl > top ? top : jl);
-            const u32 rr = (u32)(jr < 0 ? 0 : jr > top ? top : jr);
-            // exclusive prefix of the histogram (4 bins per thread)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) t += h[q];
-            u32 incl = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= (u32)o) incl += y;
-            }
-            if (lane == 31) sm.warp_sum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) { // exclusive scan of the 32 warp totals
-                const u32 v = sm.warp_sum[lane];
-                u32 wi = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const u32 y = __shfl_up_sync(0xffffffffu, wi, o);
-                    if (lane >= (u32)o) wi += y;
-                }
-                sm.warp_sum[lane] = wi - v;
-            }
-            __syncthreads();
-            u32 run = sm.warp_sum[warp] + incl - t;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const u32 b = tid * 4 + q;
-                // bin holding sample rank rl / rr
-                if (h[q] && rl >= run && rl < run + h[q]) {
-                    sm.bin[0] = b;
-                    sm.base[0] = run;
-                    sm.cnt[0] = h[q];
-                }
-                if (h[q] && rr >= run && rr < run + h[q]) {
-                    sm.bin[1] = b;
-                    sm.base[1] = run;
-                    sm.cnt[1] = h[q];
-                }
-                run += h[q];
-            }
-            if (tid == 0) {
-                sm.want[0] = 0;
-                sm.want[1] = 0;
-            }
-            __syncthreads();
-            // gather the two bins (one region if they coincide)
-            const u32 sh = hist_shift(lo, hi);
-            const u32 b0 = sm.bin[0], b1 = sm.bin[1];
-            const bool same = b0 == b1;
-            const u32 off1 = same ? 0 : sm.cnt[0];
-            const ct* samp = static_cast<const ct*>(a.samp);
-            constexpr int U = KW == 32 ? 8 : 4; // loads in flight per thread
-            for (u32 base = 0; base < kept; base += PIV_NT * U) {
-                ct cv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const u32 i = base + u * PIV_NT + tid;
-                    cv[u] = i < kept ? samp[i] : (ct)0;
-                }
-                // one slot reservation per warp and bin for all U elements
-                u32 m0 = 0, m1 = 0;
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const u32 i = base + u * PIV_NT + tid;
-                    const u32 b = i < kept ? hist_bin(cv[u], lo, sh) : 0xFFFFFFFFu;
-                    m0 |= (u32)(b == b0) << u;
-                    m1 |= (u32)(!same && b == b1) << u;
-                }
-                const u32 cnt = (u32)__popc(m0) | ((u32)__popc(m1) << 16);
-                u32 incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= (u32)o) incl += y;
-                }
-                const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
-                u32 w0 = 0, w1 = 0;
-                if (lane == 31) {
-                    if (tot & 0xFFFFu) w0 = atomicAdd(&sm.want[0], tot & 0xFFFFu);
-                    if (tot >> 16) w1 = atomicAdd(&sm.want[1], tot >> 16);
-                }
-                u32 s0 = __shfl_sync(0xffffffffu, w0, 31) + ((incl - cnt) & 0xFFFFu);
-                u32 s1 = __shfl_sync(0xffffffffu, w1, 31) + ((incl - cnt) >> 16);
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    if ((m0 >> u) & 1u) {
-                        if (s0 < sm.cnt[0] && s0 < Lim<KW>::ELEMS) sm.buf[s0] = cv[u];
-                        ++s0;
-                    }
-                    if ((m1 >> u) & 1u) {
-                        if (s1 < sm.cnt[1] && off1 + s1 < Lim<KW>::ELEMS) sm.buf[off1 + s1] = cv[u];
-                        ++s1;
-                    }
-                }
-            }
-            __syncthreads();
-            const bool consistent = sm.cnt[0] > 0 && sm.want[0] == sm.cnt[0] &&
-                                    (same || (sm.cnt[1] > 0 && sm.want[1] == sm.cnt[1])) &&
-                                    sm.cnt[0] + (same ? 0 : sm.cnt[1]) <= Lim<KW>::ELEMS;
-            const bool small = sm.cnt[0] <= WARP_SELECT_MAX && (same || sm.cnt[1] <= WARP_SELECT_MAX);
-            if (consistent && small) {
-                // two warps select the two pivots concurrently
-                if (warp < 2) {
-                    const u32 t = warp;
-                    const u32 region = (t == 1 && !same) ? 1 : 0;
-                    const ct* base = sm.buf + (region ? off1 : 0);
-                    const u32 rk = (t == 0 ? rl : rr) - sm.base[region];
-                    const ct res = warp_select_rank<KW>(base, sm.cnt[region], rk, sm.whist[t]);
-                    if (lane == 0) sm.wres[t] = res;
-                }
-                __syncthreads();
-                if (jl >= 0) pl = sm.wres[0];
-                if (jr <= top) pr = sm.wres[1];
-            } else if (consistent) {
-                if (same) {
-                    const u32 rk[2] = {rl - sm.base[0], rr - sm.base[0]};
-                    block_select_ranks<KW, 2>(sm.buf, sm.cnt[0], rk, sm.rs2);
-                    if (jl >= 0) pl = sm.rs2.result[0];
-                    if (jr <= top) pr = sm.rs2.result[1];
-                } else {
-                    const u32 rk0[1] = {rl - sm.base[0]};
-                    block_select_ranks<KW, 1>(sm.buf, sm.cnt[0], rk0, sm.rs1);
-                    if (jl >= 0) pl = sm.rs1.result[0];
-                    const u32 rk1[1] = {rr - sm.base[1]};
-                    block_select_ranks<KW, 1>(sm.buf + off1, sm.cnt[1], rk1, sm.rs1);
-                    if (jr <= top) pr = sm.rs1.result[0];
-                }
-            } else if (tid == 0) {
-                g->overflows++; // histogram and sample disagree: fall back to collecting the window
-            }
-        }
-        if (tid == 0) {
-            g->pl = (u128)pl;
-            g->pr = (u128)pr;
-            g->dst = s.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
-            g->cnt_a = 0;
-            g->cnt_b = 0;
-            g->pending = 1;
-            g->level = s.level + 1;
-            g->levels_grid++;
-            if (s.level == 0) g->sample_kept = kept;
-            // many a-elements expected: the pass compacts with block scans
-            g->dense = (jl >= 0 && kept > 0 && (double)(jl + 1) > (double)kept / 16.0) ? 1u : 0u;
-        }
-    }
-    __syncthreads();
-    for (u32 i = tid; i < HIST_BINS; i += PIV_NT) a.hist[i] = 0;
-    if (tid == 0) *a.samp_count = 0;
-}
 
 // ---- partition + reduction + branch (whole grid)
 
@@ -807,155 +489,412 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     if (threadIdx.x == 0) pass_epilogue(a);
 }
 
-// ---- one-launch selection of a small input: the first level's steps in
-// one cooperative kernel of one block per SM, separated by a bounded grid
-// barrier, then the exact finish in block 0.  For inputs of up to SMALL_MAX
-// keys the separate launches of the grid levels cost more than their work.
+// ---- the recursion levels in one cooperative launch
+// One block per SM, all resident at once.  A level is
+//   the sample (every block draws its share of the draws)
+//   -> grid barrier ->
+//   the pivots, read off the sample by every block alike (the same multiset
+//   and the same rule give the same pivots), and the pass over the source:
+//   a to the output, b to the other candidate buffer
+//   -> grid barrier ->
+//   the branch of Algorithm "select", taken by every block alike from the
+//   pass counters.
+// Levels repeat while the source holds more than G elements; block 0 then
+// finishes (levels inside the block while more than T remain, then the exact
+// selection).  The whole selection of an input of up to SMALL_MAX keys is one
+// launch.  The counters of a level are indexed by its parity, so block 0
+// clears the next level's while slower blocks may still read this level's; a
+// barrier separates the two uses.
 constexpr u64 SMALL_MAX = 1ull << 22;
 constexpr int SMALL_NT = 512;
 constexpr u64 GRID_BARRIER_NS = 200ull * 1000 * 1000;
+constexpr u32 COOP_MAX_LEVELS = 32;
 template <int KW> using SmallSmem = BlockSmem<KW, SMALL_NT>;
 
-// Every block of the grid arrives, then waits (at most `limit_ns`) until all
-// have: words[0] counts arrivals and is reset by the last one, which then
-// advances the generation words[1].  False after a timeout.
-__device__ __forceinline__ bool grid_barrier(u32* words, u64 limit_ns) {
+// Grid barrier on an arrival count that only grows (zero when the launch
+// starts): the e-th barrier of the launch is passed once the count reaches
+// e * gridDim.x.  `epoch` is thread 0's count of barriers so far.  Waits at
+// most `limit_ns`; false after a timeout.
+__device__ __forceinline__ bool grid_barrier(u32* count, u32& epoch, u64 limit_ns) {
     __shared__ u32 s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile u32* gen = words + 1;
-        const u32 g0 = *gen;
-        __threadfence();
-        bool ok = true;
-        if (atomicAdd(words, 1u) == gridDim.x - 1) {
-            atomicExch(words, 0u);
-            __threadfence();
-            atomicAdd(words + 1, 1u);
-        } else {
+        const u32 target = (++epoch) * gridDim.x;
+        __threadfence(); // this block's writes before its arrival
+        bool ok = atomicAdd(count, 1u) + 1u >= target;
+        if (!ok) {
             u64 t0, t;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-            while (*gen == g0) {
-                __nanosleep(64);
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                if (t - t0 > limit_ns) {
-                    ok = false;
+            for (;;) {
+                u32 c;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(count) : "memory");
+                if (c >= target) {
+                    ok = true;
                     break;
                 }
+                __nanosleep(32);
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                if (t - t0 > limit_ns) break;
             }
         }
-        __threadfence();
+        __threadfence(); // the other blocks' writes before this block's reads
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
 }
 
-template <int DT> __global__ void __launch_bounds__(SMALL_NT, 1) k_small(SelArgs a) {
+// Number of draws of a level: the sample size, more for a narrowed window
+// (proportionally, at most SMP_MAX_SCALE times), so that about as many land
+// inside it.
+__device__ __forceinline__ u32 level_draws(const SelArgs& a, const SelState& s) {
+    u32 draws = a.sample;
+    if (s.m_win < s.m_src) {
+        u64 ratio = s.m_src / (s.m_win ? s.m_win : 1);
+        ratio = ratio < 1 ? 1 : ratio > SMP_MAX_SCALE ? SMP_MAX_SCALE : ratio;
+        draws = (u32)((u64)draws * ratio);
+    }
+    return draws;
+}
+
+// Slots of the sample array a level fills: every draw when they all fit
+// (draw j at slot j), else the draws inside the window (appended, up to the
+// capacity).  `count` is the append counter.
+__device__ __forceinline__ u32 sample_stored(const SelArgs& a, u32 draws, const u32* count) {
+    if (draws <= a.samp_cap) return draws;
+    const u32 c = *(const volatile u32*)count;
+    return c < a.samp_cap ? c : a.samp_cap;
+}
+
+// The sample of one level, drawn by a grid of NT-thread blocks: draw j falls
+// in partition j mod p at a position uniform in it (Philox4x32-10 of counter
+// (4 floor(j / 4), level, salt, 0), word j mod 4).  When the draws fit the
+// sample array, draw j is stored at slot j (a draw outside the window as the
+// all-ones composite, which no element has); otherwise the draws inside the
+// window are appended (one reservation per warp on `count`).  The four draws
+// of one Philox block go to one thread; consecutive blocks of draws go to
+// consecutive thread blocks.
+template <int DT, int NT>
+__device__ void sample_draws(const SelArgs& a, const SelState& s, typename Comp<Key<DT>::KW>::t lo,
+                             typename Comp<Key<DT>::KW>::t hi, u32 draws, u32* count) {
     typedef Key<DT> K;
-    typedef typename K::raw_t raw_t;
     typedef typename K::key_t key_t;
+    constexpr int KW = K::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    const bool direct = draws <= a.samp_cap;
+    const u32 m = (u32)s.m_src; // sources hold fewer than 2^32 elements
+    const u32 p = a.parts < m ? a.parts : m;
+    const u32 len = m / p, rem = m - len * p;
+    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, m);
+    const CandSrc<KW> csrc{static_cast<const key_t*>(a.cand_key[s.src == SRC_CAND1 ? 1 : 0]),
+                           a.cand_idx[s.src == SRC_CAND1 ? 1 : 0], m};
+    ct* samp = static_cast<ct*>(a.samp);
+    const u32 blocks4 = (draws + 3) / 4; // Philox blocks
+    // Philox block b = (round * NT + t) * gridDim.x + blockIdx.x for thread t
+    const u32 rounds = (blocks4 + gridDim.x * NT - 1) / (gridDim.x * NT);
+    for (u32 rd = 0; rd < rounds; ++rd) {
+        const u32 b = (rd * NT + threadIdx.x) * gridDim.x + blockIdx.x;
+        // warps whose blocks of draws all lie beyond the last stop here
+        const u32 warp_b0 = (rd * NT + (threadIdx.x & ~31u)) * gridDim.x + blockIdx.x;
+        if (warp_b0 >= blocks4) break;
+        ct c[4];
+        u32 keepm = 0;
+        const u32 j0 = b * 4;
+        if (b < blocks4) {
+            const Philox4 r = philox4x32_10(j0, s.level, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const u32 j = j0 + q;
+                const u32 part = j % p;
+                const u32 plo = part * len + (part < rem ? part : rem);
+                const u32 psz = len + (part < rem ? 1 : 0);
+                const u32 pos = plo + (u32)(((u64)r.v[q] * psz) >> 32);
+                key_t kq = 0;
+                u32 x = 0;
+                if (j < draws) {
+                    if (s.src == SRC_INPUT) isrc.at(pos, kq, x);
+                    else csrc.at(pos, kq, x);
+                }
+                c[q] = C::make(kq, x);
+                keepm |= (u32)(j < draws && c[q] >= lo && c[q] <= hi) << q;
+            }
+        }
+        if (direct) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (b < blocks4 && j0 + q < draws) samp[j0 + q] = ((keepm >> q) & 1u) ? c[q] : ~(ct)0;
+        } else {
+            u32 slot = warp_reserve((u32)__popc(keepm), count);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if ((keepm >> q) & 1u) {
+                    if (slot < a.samp_cap) samp[slot] = c[q];
+                    ++slot;
+                }
+            }
+        }
+    }
+}
+
+// Pivots from the sample (one block of NT threads): the sample array
+// (`stored` slots) into shared memory `buf` by one bulk copy (completion on
+// the block's mbarrier `mb`, phase `mphase`), the number `kept` of draws in
+// the window and their smallest and largest composite; then the sample
+// elements of ranks k|S|/n -/+ Delta (pivot_ranks), selected with a histogram
+// over [smallest, largest].  Returns kept; pl / pr stay as given when a rank
+// falls outside the sample; *jl_out receives the lower rank.  `ok` turns
+// false if the copy did not complete in time.
+template <int DT, int NT>
+__device__ u32 sample_pivots(const SelArgs& a, const SelState& s, u32 stored, typename Comp<Key<DT>::KW>::t lo,
+                             typename Comp<Key<DT>::KW>::t hi, typename Comp<Key<DT>::KW>::t* buf,
+                             HistSelSmem<Key<DT>::KW>& hs, uint64_t* mb, u32& mphase, bool& ok,
+                             typename Comp<Key<DT>::KW>::t& pl, typename Comp<Key<DT>::KW>::t& pr,
+                             long long* jl_out) {
+    constexpr int KW = Key<DT>::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    __shared__ ct s_mn[NT / 32], s_mx[NT / 32];
+    __shared__ u32 s_cnt[NT / 32];
+    __shared__ long long s_jl, s_jr;
+    __shared__ u32 s_kept;
+    const u32 tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
+    // the sample array holds a whole number of 16-byte words and starts on
+    // a 16-byte boundary, as does the shared copy
+    const u32 bytes = (u32)((stored * sizeof(ct) + 15) & ~(size_t)15);
+    __syncthreads(); // earlier readers of the shared sample are done
+    if (tid == 0 && bytes > 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(mb, bytes);
+        bulk_g2s(buf, a.samp, bytes, mb);
+    }
+    if (bytes > 0) {
+        if (!mbar_wait_bounded(mb, mphase, WAIT_LIMIT_NS)) {
+            ok = false;                                          // reported, and once more
+            (void)mbar_wait_bounded(mb, mphase, WAIT_LIMIT_NS); // for the copy in flight
+        }
+        mphase ^= 1u;
+    }
+    if (__syncthreads_or(ok ? 0 : 1)) ok = false; // the same answer in every thread
+    ct mn = ~(ct)0, mx = 0;
+    u32 cnt = 0;
+    for (u32 i = tid; i < stored; i += NT) {
+        const ct c = buf[i];
+        // (a window's upper end may be the all-ones composite itself, so the
+        // stand-in for a draw outside it is excluded by value)
+        const bool in = c != ~(ct)0 && c >= lo && c <= hi;
+        cnt += (u32)in;
+        if (in && c < mn) mn = c;
+        if (in && c > mx) mx = c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ct omn = shfl_comp(mn, lane ^ (u32)o), omx = shfl_comp(mx, lane ^ (u32)o);
+        mn = omn < mn ? omn : mn;
+        mx = omx > mx ? omx : mx;
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+        s_mn[warp] = mn;
+        s_mx[warp] = mx;
+        s_cnt[warp] = cnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ct a_mn = s_mn[0], a_mx = s_mx[0];
+        u32 a_cnt = s_cnt[0];
+        for (u32 w = 1; w < NT / 32; ++w) {
+            a_mn = s_mn[w] < a_mn ? s_mn[w] : a_mn;
+            a_mx = s_mx[w] > a_mx ? s_mx[w] : a_mx;
+            a_cnt += s_cnt[w];
+        }
+        long long jl = -1, jr = 0;
+        if (a_cnt > 0) pivot_ranks(a_cnt, s.m_win, s.k_rem, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
+        s_jl = jl;
+        s_jr = jr;
+        s_kept = a_cnt;
+        s_mn[0] = a_mn;
+        s_mx[0] = a_mx;
+    }
+    __syncthreads();
+    const u32 kept = s_kept;
+    const long long jl = s_jl, jr = s_jr, top = (long long)kept - 1;
+    if (jl_out) *jl_out = jl;
+    if (kept > 0 && ok) {
+        ct x0, x1;
+        block_select_two<KW, NT>(buf, stored, s_mn[0], s_mx[0], (u32)(jl < 0 ? 0 : jl > top ? top : jl),
+                                 (u32)(jr < 0 ? 0 : jr > top ? top : jr), hs, x0, x1);
+        if (jl >= 0) pl = x0;
+        if (jr <= top) pr = x1;
+    }
+    return kept;
+}
+
+// ---- pickPivots, part 1 (whole grid): the level's draws into the sample
+// array (sample_draws).
+template <int DT> __global__ void __launch_bounds__(SMP_NT) k_sample(SelArgs a, int first) {
+    grid_dep_wait();
+    grid_dep_release();
+    typedef Comp<Key<DT>::KW> C;
+    const SelState s = first ? initial_state<DT>(a) : *a.st;
+    if (s.phase != PH_RUN || s.m_src <= a.grid_G || s.m_win <= a.finish_T) return;
+    sample_draws<DT, SMP_NT>(a, s, C::from128(s.lo), C::from128(s.hi), level_draws(a, s), a.samp_count);
+}
+
+// ---- pickPivots, part 2 (one block): the pivots from the sample
+// (sample_pivots), then the next pass armed; the sample count is left at zero
+// for the next level.  A window of at most T elements is collected whole.
+template <int KW> struct PivotSmem {
+    typedef typename Comp<KW>::t ct;
+    ct buf[Lim<KW>::ELEMS];
+    HistSelSmem<KW> hs;
+};
+
+template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, int first) {
+    grid_dep_wait();
+    grid_dep_release();
+    constexpr int KW = Key<DT>::KW;
+    typedef Comp<KW> C;
+    typedef typename C::t ct;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto& sm = *reinterpret_cast<PivotSmem<KW>*>(smem_raw);
+    __shared__ __align__(8) uint64_t mb; // completion of the sample's bulk copy
+    __shared__ u32 s_go;
+    SelState* g = a.st;
+    const u32 tid = threadIdx.x;
+    const SelState s = first ? initial_state<DT>(a) : *g;
+    if (tid == 0) {
+        if (first) *g = s;
+        u32 go = s.phase == PH_RUN;
+        if (go && s.m_src <= a.grid_G) {
+            g->phase = PH_FINISH;
+            go = 0;
+        }
+        s_go = go;
+        mbar_init(&mb, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (!s_go) return;
+    const ct lo = C::from128(s.lo), hi = C::from128(s.hi);
+    ct pl = lo, pr = hi; // "collect": every window element becomes a candidate
+    u32 kept = 0, mphase = 0;
+    long long jl = -1;
+    bool ok = true;
+    if (s.m_win > a.finish_T) {
+        const u32 stored = sample_stored(a, level_draws(a, s), a.samp_count);
+        kept = sample_pivots<DT, PIV_NT>(a, s, stored, lo, hi, sm.buf, sm.hs, &mb, mphase, ok, pl, pr, &jl);
+    }
+    if (tid == 0) {
+        if (!ok) {
+            latch(a.err, ST_ETIMEOUT);
+            g->phase = PH_ERROR;
+        }
+        g->pl = (u128)pl;
+        g->pr = (u128)pr;
+        g->dst = s.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
+        g->cnt_a = 0;
+        g->cnt_b = 0;
+        g->pending = 1;
+        g->level = s.level + 1;
+        g->levels_grid++;
+        if (s.level == 0) g->sample_kept = kept;
+        // many a-elements expected: the pass compacts with block scans (on
+        // the first level the host has chosen, by the same rule, the one
+        // variant it launches)
+        g->dense = (s.level == 0 && a.first_dense >= 0)
+                       ? (u32)a.first_dense
+                       : (jl >= 0 && kept > 0 && (double)(jl + 1) > (double)kept / 16.0) ? 1u : 0u;
+        *a.samp_count = 0;
+    }
+}
+
+template <int DT> __global__ void __launch_bounds__(SMALL_NT, 1) k_levels(SelArgs a) {
+    typedef Key<DT> K;
     constexpr int KW = K::KW;
     typedef Comp<KW> C;
     typedef typename C::t ct;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto& sm = *reinterpret_cast<SmallSmem<KW>*>(smem_raw);
+    __shared__ __align__(16) SelState ss; // this block's copy of the state, the same in every block
+    __shared__ __align__(8) uint64_t mb; // completion of the sample's bulk copy
+    CoopWords* cw = reinterpret_cast<CoopWords*>(a.gbar);
+    u32* bar = &cw->bar[0];
+    u32 epoch = 0, mphase = 0;
     SelState* g = a.st;
     const u32 tid = threadIdx.x;
-    const u32 m = (u32)a.n;
-    const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, a.n);
-    // 1. the sample: draw j falls in partition j mod p (an equal share per
-    //    partition) at a position uniform in it (Philox4x32-10 word j mod 4 of
-    //    counter (j / 4, 0, salt, 0)); every draw lies in the first window
-    const u32 s = a.sample;
-    const u32 p = a.parts < m ? a.parts : m;
-    const u32 len = m / p, rem = m - len * p;
-    ct* samp = static_cast<ct*>(a.samp);
-    for (u32 j = blockIdx.x * SMALL_NT + tid; j < s; j += gridDim.x * SMALL_NT) {
-        const Philox4 r = philox4x32_10(j >> 2, 0, 0x53414D50u, 0, (u32)a.seed, (u32)(a.seed >> 32));
-        const u32 part = j % p;
-        const u32 plo = part * len + (part < rem ? part : rem);
-        const u32 psz = len + (part < rem ? 1 : 0);
-        const u32 pos = plo + (u32)(((u64)r.v[j & 3] * psz) >> 32);
-        key_t kq;
-        u32 x;
-        isrc.at(pos, kq, x);
-        samp[j] = C::make(kq, x);
-    }
-    if (blockIdx.x == 0 && tid == 0) {
-        *g = initial_state<DT>(a);
-        g->phase = PH_RUN;
-    }
-    if (!grid_barrier(a.gbar, GRID_BARRIER_NS)) {
-        if (tid == 0) latch(a.err, ST_ETIMEOUT);
-        return;
-    }
-    // 2. the pivots, in every block alike: the sample elements of ranks
-    //    k|S|/n -/+ Delta (the same rule as the grid levels)
-    {
-        // the whole sample into shared memory, 16-byte loads, all in flight
-        // (s * sizeof(ct) is a multiple of 16 bytes: s is at least 64)
-        constexpr u32 PER = (Lim<KW>::ELEMS * sizeof(ct) / 16 + SMALL_NT - 1) / SMALL_NT;
-        const uint4* src4 = reinterpret_cast<const uint4*>(samp);
-        uint4* dst4 = reinterpret_cast<uint4*>(sm.samp);
-        const u32 n4 = (u32)((s * sizeof(ct)) / 16);
-        uint4 v[PER];
-#pragma unroll
-        for (u32 q = 0; q < PER; ++q) {
-            const u32 i = q * SMALL_NT + tid;
-            if (i < n4) v[q] = __ldcg(src4 + i);
-        }
-#pragma unroll
-        for (u32 q = 0; q < PER; ++q) {
-            const u32 i = q * SMALL_NT + tid;
-            if (i < n4) dst4[i] = v[q];
-        }
-    }
     if (tid == 0) {
-        long long jl, jr;
-        pivot_ranks(s, a.n, a.k, a.z, (a.flags & TOPK_FLAG_RAW_DELTA) != 0, jl, jr);
-        sm.jl = jl;
-        sm.jr = jr;
+        ss = initial_state<DT>(a);
+        mbar_init(&mb, 1);
+        mbar_fence_init();
     }
     __syncthreads();
-    const ct lo = 0, hi = C::from128(key_domain_max<DT>());
-    const long long jl = sm.jl, jr = sm.jr, top = (long long)s - 1;
-    ct pl = lo, pr = hi;
-    if (jl >= 0) pl = block_select_hist<KW, SMALL_NT>(sm.samp, s, lo, hi, (u32)(jl > top ? top : jl), sm.hs);
-    if (jr <= top) pr = block_select_hist<KW, SMALL_NT>(sm.samp, s, lo, hi, (u32)(jr < 0 ? 0 : jr), sm.hs);
-    // 3. the pass: a to the output, b to the candidate buffer
-    {
-        Sink<DT> sink;
-        sink.out_keys = static_cast<raw_t*>(a.out_keys);
-        sink.out_idx = a.out_idx;
-        sink.out_base = 0;
-        sink.cap_a = a.k;
-        sink.ck = static_cast<key_t*>(a.cand_key[0]);
-        sink.ci = a.cand_idx[0];
-        sink.cap_b = a.cap_b;
-        sink.cnt_a = &g->cnt_a;
-        sink.cnt_b = &g->cnt_b;
-        if (pl > lo) pass_tiles<SMALL_NT, true, false, DT>(isrc, blockIdx.x, gridDim.x, lo, pl, pr, sink, sm.ps);
-        else pass_tiles<SMALL_NT, false, false, DT>(isrc, blockIdx.x, gridDim.x, lo, pl, pr, sink, sm.ps);
+    bool ok = true;
+    for (u32 lv = 0; lv < COOP_MAX_LEVELS && ss.m_src > a.grid_G; ++lv) {
+        const u32 par = lv & 1u;
+        const ct lo = C::from128(ss.lo), hi = C::from128(ss.hi);
+        const bool collect = ss.m_win <= a.finish_T; // every window element becomes a candidate
+        const u32 draws = level_draws(a, ss);
+        // 1. the sample
+        if (!collect) sample_draws<DT, SMALL_NT>(a, ss, lo, hi, draws, &cw->scnt[par]);
+        if (!grid_barrier(bar, epoch, GRID_BARRIER_NS)) {
+            ok = false;
+            break;
+        }
+        // 2. the pivots (every block alike), then the pass
+        if (blockIdx.x == 0 && tid == 0) {
+            cw->scnt[par ^ 1u] = 0;
+            cw->cnt_a[par ^ 1u] = 0;
+            cw->cnt_b[par ^ 1u] = 0;
+        }
+        ct pl = lo, pr = hi;
+        u32 kept = 0;
+        if (!collect) {
+            const u32 stored = sample_stored(a, draws, &cw->scnt[par]);
+            kept = sample_pivots<DT, SMALL_NT>(a, ss, stored, lo, hi, sm.samp, sm.hs, &mb, mphase, ok, pl, pr,
+                                               nullptr);
+            if (!ok) break; // (block-uniform)
+        }
+        if (tid == 0) {
+            ss.pl = (u128)pl;
+            ss.pr = (u128)pr;
+            ss.dst = ss.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
+        }
+        __syncthreads();
+        run_pass_to<SMALL_NT, DT, false, false>(a, ss, blockIdx.x, gridDim.x, sm.ps, &cw->cnt_a[par],
+                                                &cw->cnt_b[par]);
+        if (!grid_barrier(bar, epoch, GRID_BARRIER_NS)) {
+            ok = false;
+            break;
+        }
+        // 3. the branch (every block alike)
+        if (tid == 0) {
+            if (ss.level == 0) ss.sample_kept = kept;
+            ss.cnt_a = __ldcg(&cw->cnt_a[par]);
+            ss.cnt_b = __ldcg(&cw->cnt_b[par]);
+            ss.pending = 1;
+            ss.level += 1;
+            ss.levels_grid += 1;
+            decide(ss);
+        }
+        __syncthreads();
     }
-    if (!grid_barrier(a.gbar, GRID_BARRIER_NS)) {
+    if (!ok) {
         if (tid == 0) latch(a.err, ST_ETIMEOUT);
         return;
     }
-    // 4. block 0: the branch of Algorithm "select", then the finish
     if (blockIdx.x != 0) return;
+    // block 0: the state for the finish (and the statistics), then the finish
     if (tid == 0) {
-        g->pl = (u128)pl;
-        g->pr = (u128)pr;
-        g->dst = SRC_CAND0;
-        g->pending = 1;
-        g->level = 1;
-        g->levels_grid = 1;
-        g->sample_kept = s;
-        g->cnt_a = *(volatile u64*)&g->cnt_a;
-        g->cnt_b = *(volatile u64*)&g->cnt_b;
-        decide(*g);
+        if (ss.m_src > a.grid_G) { // more levels than any input needs
+            ss.status = ST_EINTERNAL;
+            ss.phase = PH_ERROR;
+            latch(a.err, ST_EINTERNAL);
+        }
+        *g = ss;
     }
     __syncthreads();
+    if (ss.phase != PH_RUN) return;
     block_levels_and_finish<DT, true, true>(a, sm);
 }
 
@@ -1117,6 +1056,7 @@ static SelArgs make_args(const void* keys, u64 n, u64 k, void* out_keys, u32* ou
     a.z = tu.z;
     a.flags = tu.flags;
     a.aligned = (reinterpret_cast<uintptr_t>(keys) & 15u) == 0;
+    a.first_dense = -1; // decided on the device unless the host fixes it
     return a;
 }
 
@@ -1150,7 +1090,7 @@ template <int DT> static topk_status set_smem_attrs() {
                              (int)sizeof(PivotSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
     if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_small<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_levels<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(SmallSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
     done_mask.fetch_or(bit);
@@ -1182,13 +1122,13 @@ template <int DT> static int pass_grid(int sms, bool first) {
     return sms * (first ? occ_first : occ_rest);
 }
 
-// Whether one block of k_small fits on every SM (the cooperative launch
+// Whether one block of k_levels fits on every SM (the cooperative launch
 // needs the whole grid resident).
 template <int DT> static bool small_fits(int sms) {
     static int occ = -1;
     if (occ < 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_small<DT>, SMALL_NT, sizeof(SmallSmem<Key<DT>::KW>)) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_levels<DT>, SMALL_NT, sizeof(SmallSmem<Key<DT>::KW>)) !=
             cudaSuccess) {
             cudaGetLastError();
             o = 0;
@@ -1197,6 +1137,17 @@ template <int DT> static bool small_fits(int sms) {
     }
     (void)sms;
     return occ >= 1;
+}
+
+// Pass mode of the first level: dense when more than 1/16 of the sample is
+// expected below the lower pivot.  The first level's sample is `s` draws, all
+// inside its window, so its pivot ranks are known before the launch; the
+// mode only steers the pass (both modes give the same result).
+static bool first_level_dense(u64 n, u64 k, u32 s, float z, bool raw) {
+    const double mu = (double)s * (double)k / (double)n;
+    const double d = raw ? z : z * std::sqrt(std::max(0.0, mu * (1.0 - mu / s))) + z * z / 3.0 + 1.0;
+    const double jl = std::floor(mu - d) - 1.0;
+    return jl >= 0.0 && jl + 1.0 > (double)s / 16.0;
 }
 
 // Candidate capacity for a first level over n keys: twice the expected
@@ -1230,13 +1181,27 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     }
     topk_status rs = set_smem_attrs<DT>();
     if (rs != TOPK_OK) return rs;
-    // the first level's expected bracket fits the finishing block
-    if (n <= SMALL_MAX && n > tu.G && a.gbar != nullptr && (!ctx || ctx->one_launch) && small_fits<DT>(sms) &&
-        1.2 * est_bracket(n, k, tu.sample, tu.z) <= (double)tu.T) {
-        // one launch: sample, pivots, pass and finish (cooperative, one block per SM)
+    // inputs of up to SMALL_MAX keys: one cooperative launch of one block per
+    // SM (k_levels); contexts whose work shares the GPU with other kernels
+    // (the serving slots) keep to ordinary launches, which never wait for a
+    // whole idle GPU
+    const bool coop = n > tu.G && n <= SMALL_MAX && a.gbar != nullptr && (!ctx || ctx->one_launch) &&
+                      small_fits<DT>(sms);
+    // the first level's pass mode, fixed here so that one variant is launched
+    const bool bulk = a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY);
+    a.first_dense =
+        bulk ? (first_level_dense(n, k, tu.sample, tu.z, (tu.flags & TOPK_FLAG_RAW_DELTA) != 0) ? 1 : 0) : -1;
+    auto first_pass = [&]() -> cudaError_t {
+        if (!bulk) return launch_dep(k_pass_first<DT>, pass_grid<DT>(sms, true), PASS_NT, 0, st, a);
+        if (a.first_dense)
+            return launch_dep(k_pass_tma<DT, true>, tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st, a);
+        return launch_dep(k_pass_tma<DT, false>, tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st, a);
+    };
+    if (coop) {
+        // the whole selection in one launch: every level and the finish
         if (ctx) profile_pass_begin(ctx, st);
-        cudaError_t e = cudaMemsetAsync(a.gbar, 0, 2 * sizeof(u32), st);
-        if (e == cudaSuccess) e = launch_coop(k_small<DT>, sms, SMALL_NT, sizeof(SmallSmem<KW>), st, a);
+        cudaError_t e = cudaMemsetAsync(a.gbar, 0, sizeof(CoopWords), st);
+        if (e == cudaSuccess) e = launch_coop(k_levels<DT>, sms, SMALL_NT, sizeof(SmallSmem<KW>), st, a);
         if (e != cudaSuccess) return cuda_status(e);
         if (ctx) {
             profile_pass_end(ctx, st);
@@ -1261,20 +1226,14 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
         if (e == cudaSuccess) e = launch_dep(k_pivots<DT>, 1, PIV_NT, sizeof(PivotSmem<KW>), st, a, l == 0 ? 1 : 0);
         if (e != cudaSuccess) return cuda_status(e);
         if (l == 0 && ctx) profile_pass_begin(ctx, st);
-        if (l == 0 && a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY)) {
-            // the mode is chosen on the device: the variant that does not match returns at once
-            e = launch_dep(k_pass_tma<DT, false>, tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st, a);
-            if (e == cudaSuccess)
-                e = launch_dep(k_pass_tma<DT, true>, tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st, a);
-        }
-        else if (l == 0) e = launch_dep(k_pass_first<DT>, pass_grid<DT>(sms, true), PASS_NT, 0, st, a);
+        if (l == 0) e = first_pass();
         else e = launch_dep(k_pass<DT>, pass_grid<DT>(sms, false), PASS_NT, 0, st, a);
         if (e != cudaSuccess) return cuda_status(e);
         if (l == 0 && ctx) profile_pass_end(ctx, st);
     }
     const cudaError_t e = launch_dep(k_finish<DT>, 1, BLK_NT, smem, st, a, levels == 0 ? 1 : 0);
     if (e != cudaSuccess) return cuda_status(e);
-    if (ctx) count_launch(ctx, 3 * (uint64_t)levels + 1 + (levels > 0 && a.aligned ? 1 : 0));
+    if (ctx) count_launch(ctx, 3 * (uint64_t)levels + 1);
     return cuda_status(cudaGetLastError());
 }
 
@@ -1319,7 +1278,6 @@ topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_
     a.samp_count = ctx->d_counter + 3;
     a.pass_done = ctx->d_counter + 2;
     a.gbar = ctx->d_counter + 8;
-    a.hist = ctx->d_hist;
     a.cand_key[0] = base + off_k0;
     a.cand_key[1] = base + off_k1;
     a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
@@ -1346,8 +1304,7 @@ constexpr u64 NOALLOC_MAX_N = 1ull << 22;  // largest n accepted (4 Mi keys)
 constexpr u64 NOALLOC_CAP = 1ull << 19;
 constexpr size_t NA_OFF_STATE = 0;         // SelState
 constexpr size_t NA_OFF_WORDS = 4096;      // [0] error, [1] reduction done, [2] pass done, [3] sample count
-constexpr size_t NA_OFF_HIST = 8192;       // HIST_BINS u32
-constexpr size_t NA_OFF_PART = NA_OFF_HIST + HIST_BINS * 4; // per-block composites of the k = 1 / k = n reduction
+constexpr size_t NA_OFF_PART = 8192;       // per-block composites of the k = 1 / k = n reduction
 constexpr size_t NA_PART_BYTES = 64 * 1024;
 constexpr size_t NA_OFF_SAMP = NA_OFF_PART + NA_PART_BYTES; // sample, Lim<32>::ELEMS * 8 = Lim<64>::ELEMS * 16 bytes
 constexpr size_t NA_SAMP_BYTES = 128 * 1024;
@@ -1391,11 +1348,9 @@ topk_status run_select_noalloc(char* base, int sms, const void* keys, u64 n, u64
     a.pass_done = words + 2;
     a.samp_count = words + 3;
     a.gbar = words + 8;
-    a.hist = reinterpret_cast<u32*>(base + NA_OFF_HIST);
-    // the error word, the block-done counters, the sample count and the
-    // histogram must start at zero (a call that failed may have left them set)
+    // the error word, the block-done counters and the sample count must
+    // start at zero (a call that failed may have left them set)
     if (cudaMemsetAsync(words, 0, 4 * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
-    if (cudaMemsetAsync(a.hist, 0, HIST_BINS * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
     if (d_status && cudaMemsetAsync(d_status, 0, sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;
     return enqueue_select<DT>(nullptr, a, tu, sms, words + 1, base + NA_OFF_PART, st);
 }

@@ -1,11 +1,12 @@
-"""The one-launch path of topk_select (GPU): inputs of up to 2^22 keys whose
-first bracket fits the finishing block are selected by one cooperative
-kernel (sample, pivots, pass, grid barrier, in-block finish).
+"""The one-launch path of topk_select (GPU).  Inputs of up to 2^22 keys are
+selected by one cooperative launch (every level: sample, grid barrier,
+pivots and pass, grid barrier, branch; then the in-block finish); larger
+inputs take three launches per grid level (sample, pivots, pass) and the
+finish.
 
-Each case checks that the path was taken (one kernel launch, counted by the
-context's measurement hooks) and that the result is the oracle's, bit for
-bit; the boundary cases check that the grid path takes over above 2^22 keys
-and for brackets too wide for the finishing block.
+Each case checks the launch count (counted by the context's measurement
+hooks) and that the result is the oracle's, bit for bit, including forced
+pivot failures and candidate overflows on both sides of the limit.
 """
 import numpy as np
 import pytest
@@ -58,19 +59,26 @@ def launches_of(ctx, run):
     return out, ctx.profile_read(reset=True)["launches"]
 
 
-# (key type, n, k): brackets of a few thousand keys at most (64-bit keys have
-# half the finishing block's room, so smaller k), sizes from just above the
-# one-block range to the path's limit, ragged and power-of-two
+# (key type, n, k): sizes from just above the one-block range to the path's
+# limit, ragged and power-of-two; k from 2 to n - 1 (one level, or several
+# inside the one launch)
 CASES = [
     ("u32", 16385, 2),
+    ("u32", 16385, 8192),
     ("u32", 1 << 20, 1000),
+    ("u32", 1 << 20, 1 << 19),
     ("u32", SMALL_MAX, 4000),
+    ("u32", SMALL_MAX, SMALL_MAX - 1),
     ("i32", 300007, 777),
+    ("i32", 300007, 100002),
     ("f32", (1 << 21) + 3, 100),
     ("f32", SMALL_MAX, 3000),
+    ("f32", SMALL_MAX, SMALL_MAX // 2),
     ("bf16", SMALL_MAX, 5000),
     ("bf16", 999_999, 2),
+    ("bf16", 999_999, 499_999),
     ("u64", 1_000_003, 50),
+    ("u64", 1_000_003, 333_334),
     ("u64", SMALL_MAX, 100),
 ]
 
@@ -88,22 +96,36 @@ def test_one_launch_exact(tk, ctx, orc, name, n, k):
     check_against_oracle(keys, name, k, out, orc)
 
 
-def test_grid_path_above_the_limit(tk, ctx, orc):
-    """One key more than the limit, or a bracket wider than the finishing
-    block, takes the grid levels (more than one launch), with the same
-    result rules."""
-    n = SMALL_MAX + 1
-    keys = keys_for("u32", n, seed=5)
-    d = to_device(keys, "u32")
-    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, 100))
-    assert launches > 1
-    check_against_oracle(keys, "u32", 100, out, orc)
-    n = 1 << 20
+@pytest.mark.parametrize("name,n", [("u32", SMALL_MAX + 1), ("f32", (1 << 24) + 5), ("u64", (1 << 23) + 3)])
+def test_grid_levels_above_the_limit(tk, ctx, orc, name, n):
+    """Above the limit: three launches per grid level (sample, pivots,
+    pass), then the finish."""
+    keys = keys_for(name, n, seed=5)
+    d = to_device(keys, name)
+    for k in (2, 100, 1 << 16, n // 3, n // 2, n - 1):
+        out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k))
+        assert launches > 1 and (launches - 1) % 3 == 0
+        check_against_oracle(keys, name, k, out, orc)
+
+
+def test_above_the_limit_forced_failures_and_overflows(tk, ctx, orc):
+    """Above the limit, a margin far too narrow misses rank k and candidate
+    buffers of T pairs overflow; the results stay exact."""
+    n = SMALL_MAX + 12345
     keys = keys_for("u32", n, seed=6)
     d = to_device(keys, "u32")
-    out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, n // 2))
-    assert launches > 1
-    check_against_oracle(keys, "u32", n // 2, out, orc)
+    failures = overflows = 0
+    for k in (17, 5000, n // 3, n - 5):
+        p = tk.make_params(delta_factor=0.25, flags=tk.TOPK_FLAG_RAW_DELTA)
+        out = tk.topk_select(ctx, d, k, params=p)
+        check_against_oracle(keys, "u32", k, out, orc)
+        failures += ctx.last_stats()["pivot_failures"]
+    for k in (n // 2, n // 5):
+        p = tk.make_params(flags=tk.TOPK_FLAG_TINY_CAND)
+        out = tk.topk_select(ctx, d, k, params=p)
+        check_against_oracle(keys, "u32", k, out, orc)
+        overflows += ctx.last_stats()["overflows"]
+    assert failures > 0 and overflows > 0
 
 
 def test_one_launch_forced_pivot_failures(tk, ctx, orc):
@@ -114,7 +136,7 @@ def test_one_launch_forced_pivot_failures(tk, ctx, orc):
     keys = keys_for("u32", n, seed=7)
     d = to_device(keys, "u32")
     failures = 0
-    for k in (17, 900, 3000):
+    for k in (17, 900, 3000, n // 2):
         p = tk.make_params(delta_factor=0.25, flags=tk.TOPK_FLAG_RAW_DELTA)
         out, launches = launches_of(ctx, lambda: tk.topk_select(ctx, d, k, params=p))
         assert launches == 1

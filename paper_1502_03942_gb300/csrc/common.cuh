@@ -217,17 +217,9 @@ struct SelArgs {
     u32* samp_count;          // number drawn into samp (zero between levels)
     u32* pass_done;           // block-done counter of the pass (zero between passes)
     u32 samp_cap;
-    u32* gbar;                // one-launch path: grid barrier words (arrivals, generation)
     int first_dense;          // first level's pass mode chosen by the host (0/1), or -1
 };
 
-// Words of the cooperative launch of one call (SelArgs::gbar), all zero when
-// the call starts.
-struct CoopWords {
-    u32 bar[2];             // [0] grid-barrier arrival count, [1] unused
-    u32 scnt[2];            // sample sizes, by level parity
-    u64 cnt_a[2], cnt_b[2]; // pass counters, by level parity
-};
 
 // Largest composite of a key type's domain (the first window's upper end):
 // every composite of that type is at or below it, and the window histogram

@@ -42,9 +42,6 @@ struct topk_ctx {
     uint32_t* d_counter = nullptr; // last-block-done counters (zero between calls)
     void* d_state = nullptr;       // selection state (SelState or RunsState)
     int last_kind = topk::LAST_NONE;
-    // small selections may run as one cooperative launch (off for contexts
-    // whose work shares the GPU with concurrent kernels: the serving slots)
-    bool one_launch = true;
     std::string device_name;
     // autotuned batched settings by (dtype, floor(log2(rows)))
     std::map<std::pair<int, int>, topk_params> tuned;
@@ -92,24 +89,6 @@ inline cudaError_t launch_dep(void (*kernel)(KArgs...), int grid, int block, siz
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
-
-// Cooperative launch (all blocks resident at once, so they may wait on one
-// another) on `st`.
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_coop(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t st,
-                               Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);

@@ -489,61 +489,6 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     if (threadIdx.x == 0) pass_epilogue(a);
 }
 
-// ---- the recursion levels in one cooperative launch
-// One block per SM, all resident at once.  A level is
-//   the sample (every block draws its share of the draws)
-//   -> grid barrier ->
-//   the pivots, read off the sample by every block alike (the same multiset
-//   and the same rule give the same pivots), and the pass over the source:
-//   a to the output, b to the other candidate buffer
-//   -> grid barrier ->
-//   the branch of Algorithm "select", taken by every block alike from the
-//   pass counters.
-// Levels repeat while the source holds more than G elements; block 0 then
-// finishes (levels inside the block while more than T remain, then the exact
-// selection).  The whole selection of an input of up to SMALL_MAX keys is one
-// launch.  The counters of a level are indexed by its parity, so block 0
-// clears the next level's while slower blocks may still read this level's; a
-// barrier separates the two uses.
-constexpr u64 SMALL_MAX = 1ull << 22;
-constexpr int SMALL_NT = 512;
-constexpr u64 GRID_BARRIER_NS = 200ull * 1000 * 1000;
-constexpr u32 COOP_MAX_LEVELS = 32;
-template <int KW> using SmallSmem = BlockSmem<KW, SMALL_NT>;
-
-// Grid barrier on an arrival count that only grows (zero when the launch
-// starts): the e-th barrier of the launch is passed once the count reaches
-// e * gridDim.x.  `epoch` is thread 0's count of barriers so far.  Waits at
-// most `limit_ns`; false after a timeout.
-__device__ __forceinline__ bool grid_barrier(u32* count, u32& epoch, u64 limit_ns) {
-    __shared__ u32 s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const u32 target = (++epoch) * gridDim.x;
-        __threadfence(); // this block's writes before its arrival
-        bool ok = atomicAdd(count, 1u) + 1u >= target;
-        if (!ok) {
-            u64 t0, t;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-            for (;;) {
-                u32 c;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(c) : "l"(count) : "memory");
-                if (c >= target) {
-                    ok = true;
-                    break;
-                }
-                __nanosleep(32);
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                if (t - t0 > limit_ns) break;
-            }
-        }
-        __threadfence(); // the other blocks' writes before this block's reads
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // Number of draws of a level: the sample size, more for a narrowed window
 // (proportionally, at most SMP_MAX_SCALE times), so that about as many land
 // inside it.
@@ -809,95 +754,6 @@ template <int DT> __global__ void __launch_bounds__(PIV_NT) k_pivots(SelArgs a, 
     }
 }
 
-template <int DT> __global__ void __launch_bounds__(SMALL_NT, 1) k_levels(SelArgs a) {
-    typedef Key<DT> K;
-    constexpr int KW = K::KW;
-    typedef Comp<KW> C;
-    typedef typename C::t ct;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto& sm = *reinterpret_cast<SmallSmem<KW>*>(smem_raw);
-    __shared__ __align__(16) SelState ss; // this block's copy of the state, the same in every block
-    __shared__ __align__(8) uint64_t mb; // completion of the sample's bulk copy
-    CoopWords* cw = reinterpret_cast<CoopWords*>(a.gbar);
-    u32* bar = &cw->bar[0];
-    u32 epoch = 0, mphase = 0;
-    SelState* g = a.st;
-    const u32 tid = threadIdx.x;
-    if (tid == 0) {
-        ss = initial_state<DT>(a);
-        mbar_init(&mb, 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-    bool ok = true;
-    for (u32 lv = 0; lv < COOP_MAX_LEVELS && ss.m_src > a.grid_G; ++lv) {
-        const u32 par = lv & 1u;
-        const ct lo = C::from128(ss.lo), hi = C::from128(ss.hi);
-        const bool collect = ss.m_win <= a.finish_T; // every window element becomes a candidate
-        const u32 draws = level_draws(a, ss);
-        // 1. the sample
-        if (!collect) sample_draws<DT, SMALL_NT>(a, ss, lo, hi, draws, &cw->scnt[par]);
-        if (!grid_barrier(bar, epoch, GRID_BARRIER_NS)) {
-            ok = false;
-            break;
-        }
-        // 2. the pivots (every block alike), then the pass
-        if (blockIdx.x == 0 && tid == 0) {
-            cw->scnt[par ^ 1u] = 0;
-            cw->cnt_a[par ^ 1u] = 0;
-            cw->cnt_b[par ^ 1u] = 0;
-        }
-        ct pl = lo, pr = hi;
-        u32 kept = 0;
-        if (!collect) {
-            const u32 stored = sample_stored(a, draws, &cw->scnt[par]);
-            kept = sample_pivots<DT, SMALL_NT>(a, ss, stored, lo, hi, sm.samp, sm.hs, &mb, mphase, ok, pl, pr,
-                                               nullptr);
-            if (!ok) break; // (block-uniform)
-        }
-        if (tid == 0) {
-            ss.pl = (u128)pl;
-            ss.pr = (u128)pr;
-            ss.dst = ss.src == SRC_CAND0 ? SRC_CAND1 : SRC_CAND0;
-        }
-        __syncthreads();
-        run_pass_to<SMALL_NT, DT, false, false>(a, ss, blockIdx.x, gridDim.x, sm.ps, &cw->cnt_a[par],
-                                                &cw->cnt_b[par]);
-        if (!grid_barrier(bar, epoch, GRID_BARRIER_NS)) {
-            ok = false;
-            break;
-        }
-        // 3. the branch (every block alike)
-        if (tid == 0) {
-            if (ss.level == 0) ss.sample_kept = kept;
-            ss.cnt_a = __ldcg(&cw->cnt_a[par]);
-            ss.cnt_b = __ldcg(&cw->cnt_b[par]);
-            ss.pending = 1;
-            ss.level += 1;
-            ss.levels_grid += 1;
-            decide(ss);
-        }
-        __syncthreads();
-    }
-    if (!ok) {
-        if (tid == 0) latch(a.err, ST_ETIMEOUT);
-        return;
-    }
-    if (blockIdx.x != 0) return;
-    // block 0: the state for the finish (and the statistics), then the finish
-    if (tid == 0) {
-        if (ss.m_src > a.grid_G) { // more levels than any input needs
-            ss.status = ST_EINTERNAL;
-            ss.phase = PH_ERROR;
-            latch(a.err, ST_EINTERNAL);
-        }
-        *g = ss;
-    }
-    __syncthreads();
-    if (ss.phase != PH_RUN) return;
-    block_levels_and_finish<DT, true, true>(a, sm);
-}
-
 // Remaining levels in one block, then the exact finish.
 template <int DT> __global__ void __launch_bounds__(BLK_NT) k_finish(SelArgs a, int first) {
     grid_dep_wait();
@@ -1089,9 +945,7 @@ template <int DT> static topk_status set_smem_attrs() {
     if (cudaFuncSetAttribute(k_pivots<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PivotSmem<Key<DT>::KW>)) != cudaSuccess)
         return TOPK_ECUDA;
-    if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess ||
-        cudaFuncSetAttribute(k_levels<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(SmallSmem<Key<DT>::KW>)) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_finish<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess)
         return TOPK_ECUDA;
     done_mask.fetch_or(bit);
     return TOPK_OK;
@@ -1120,23 +974,6 @@ template <int DT> static int pass_grid(int sms, bool first) {
         occ_first = std::max(1, o1);
     }
     return sms * (first ? occ_first : occ_rest);
-}
-
-// Whether one block of k_levels fits on every SM (the cooperative launch
-// needs the whole grid resident).
-template <int DT> static bool small_fits(int sms) {
-    static int occ = -1;
-    if (occ < 0) {
-        int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_levels<DT>, SMALL_NT, sizeof(SmallSmem<Key<DT>::KW>)) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            o = 0;
-        }
-        occ = o;
-    }
-    (void)sms;
-    return occ >= 1;
 }
 
 // Pass mode of the first level: dense when more than 1/16 of the sample is
@@ -1181,12 +1018,6 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
     }
     topk_status rs = set_smem_attrs<DT>();
     if (rs != TOPK_OK) return rs;
-    // inputs of up to SMALL_MAX keys: one cooperative launch of one block per
-    // SM (k_levels); contexts whose work shares the GPU with other kernels
-    // (the serving slots) keep to ordinary launches, which never wait for a
-    // whole idle GPU
-    const bool coop = n > tu.G && n <= SMALL_MAX && a.gbar != nullptr && (!ctx || ctx->one_launch) &&
-                      small_fits<DT>(sms);
     // the first level's pass mode, fixed here so that one variant is launched
     const bool bulk = a.aligned && !(tu.flags & TOPK_FLAG_NO_BULK_COPY);
     a.first_dense =
@@ -1197,18 +1028,6 @@ static topk_status enqueue_select(topk_ctx* ctx, SelArgs a, const Tuning& tu, in
             return launch_dep(k_pass_tma<DT, true>, tma_grid<DT, true>(sms), TMA_NT, TmaCfg<DT, true>::SMEM, st, a);
         return launch_dep(k_pass_tma<DT, false>, tma_grid<DT, false>(sms), TMA_NT, TmaCfg<DT, false>::SMEM, st, a);
     };
-    if (coop) {
-        // the whole selection in one launch: every level and the finish
-        if (ctx) profile_pass_begin(ctx, st);
-        cudaError_t e = cudaMemsetAsync(a.gbar, 0, sizeof(CoopWords), st);
-        if (e == cudaSuccess) e = launch_coop(k_levels<DT>, sms, SMALL_NT, sizeof(SmallSmem<KW>), st, a);
-        if (e != cudaSuccess) return cuda_status(e);
-        if (ctx) {
-            profile_pass_end(ctx, st);
-            count_launch(ctx);
-        }
-        return cuda_status(cudaGetLastError());
-    }
     // grid levels until the candidates fit the block finisher's range
     int levels = 0;
     {
@@ -1277,7 +1096,6 @@ topk_status run_select(topk_ctx* ctx, const void* keys, u64 n, u64 k, void* out_
     a.samp_cap = Lim<KW>::ELEMS;
     a.samp_count = ctx->d_counter + 3;
     a.pass_done = ctx->d_counter + 2;
-    a.gbar = ctx->d_counter + 8;
     a.cand_key[0] = base + off_k0;
     a.cand_key[1] = base + off_k1;
     a.cand_idx[0] = reinterpret_cast<u32*>(base + off_i0);
@@ -1320,7 +1138,6 @@ template <int DT> topk_status noalloc_prepare_dt(int sms) {
     (void)tma_grid<DT, false>(sms);
     (void)tma_grid<DT, true>(sms);
     (void)pass_grid<DT>(sms, true);
-    (void)small_fits<DT>(sms);
     return cudaGetLastError() == cudaSuccess ? TOPK_OK : TOPK_ECUDA;
 }
 
@@ -1347,7 +1164,6 @@ topk_status run_select_noalloc(char* base, int sms, const void* keys, u64 n, u64
     a.samp_cap = Lim<KW>::ELEMS;
     a.pass_done = words + 2;
     a.samp_count = words + 3;
-    a.gbar = words + 8;
     // the error word, the block-done counters and the sample count must
     // start at zero (a call that failed may have left them set)
     if (cudaMemsetAsync(words, 0, 4 * sizeof(u32), st) != cudaSuccess) return TOPK_ECUDA;

@@ -253,9 +253,6 @@ topk_status topk_serve_create(topk_server** out, int device, uint64_t hbm_budget
     for (Slot& slot : s->slots) {
         if (rs != TOPK_OK) break;
         if ((rs = topk_ctx_create(&slot.ctx, device)) != TOPK_OK) break;
-        // a cooperative launch would wait for room on every SM behind the
-        // other slots' kernels
-        slot.ctx->one_launch = false;
         // scratch for the largest work a slot usually gets (a selection of
         // 2^26 keys, a batch of MAX_BATCH_ROWS rows, 64-bit keys), so that
         // growing it -- which synchronises the device -- stays rare

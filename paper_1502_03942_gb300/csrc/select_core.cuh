@@ -784,6 +784,132 @@ __device__ __forceinline__ void queue_drain(WarpQ<Key<DT>::KW>& q, QState& qs, c
     __syncwarp();
 }
 
+// ---- per-lane warp queues.  Lane L's j-th entry sits at index j * 32 + L
+// of a buffer, so a lane appends its own hits with no cross-lane step (no
+// scan) and without bank conflicts; the lanes' counts differ, so flushing and
+// writing go over rows j < the warp's largest count.  Two buffers: a full one
+// is counted and its reservations issued, and it is written at the next
+// flush, so no warp waits for its atomics.
+template <int KW> struct LQ {
+    static constexpr u32 PER_LANE = WarpQ<KW>::QCAP / 32; // entries of one lane per buffer
+    static constexpr u32 CH = PER_LANE >= 8 ? 8 : 4;      // slots per chunk on the slow path
+    static_assert(PER_LANE >= CH, "a chunk of hits always fits an emptied lane");
+};
+struct LQState {
+    u32 cnt;   // this lane's entries in the active buffer
+    u32 cq;    // active buffer (warp-uniform)
+    u32 pcnt;  // this lane's entries in the other buffer still to be written
+    u32 pmax;  // largest pcnt of the warp (0: nothing pending)
+    u64 ra, rb; // lane 0: reservations of the pending entries
+    __device__ static LQState make() { return LQState{0u, 0u, 0u, 0u, 0ull, 0ull}; }
+};
+
+template <int DT>
+__device__ __forceinline__ void lq_write(const typename Comp<Key<DT>::KW>::key_t* qk, const u32* qi, u32 cnt, u32 mx,
+                                         u64 ra, u64 rb, const Sink<DT>& sink, typename Comp<Key<DT>::KW>::t lo,
+                                         typename Comp<Key<DT>::KW>::t pl, typename Comp<Key<DT>::KW>::t pr) {
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename C::t ct;
+    u64 ba = __shfl_sync(0xffffffffu, (unsigned long long)ra, 0);
+    u64 bb = __shfl_sync(0xffffffffu, (unsigned long long)rb, 0);
+    const u32 below = lanemask_lt(), lane = lane_id();
+    for (u32 j = 0; j < mx; ++j) {
+        bool isa = false, isb = false;
+        typename C::key_t kv = 0;
+        u32 iv = 0;
+        if (j < cnt) {
+            kv = qk[j * 32 + lane];
+            iv = qi[j * 32 + lane];
+            const ct c = C::make(kv, iv);
+            isa = c >= lo && c < pl;
+            isb = c >= pl && c <= pr;
+        }
+        const u32 bala = __ballot_sync(0xffffffffu, isa), balb = __ballot_sync(0xffffffffu, isb);
+        if (isa) sink.put_a(ba + __popc(bala & below), kv, iv);
+        if (isb) sink.put_b(bb + __popc(balb & below), kv, iv);
+        ba += __popc(bala);
+        bb += __popc(balb);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void lq_flush(WarpQ<Key<DT>::KW>& q, LQState& qs, const Sink<DT>& sink,
+                                         typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                         typename Comp<Key<DT>::KW>::t pr) {
+    typedef Comp<Key<DT>::KW> C;
+    typedef typename C::t ct;
+    __syncwarp();
+    if (qs.pmax) lq_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pcnt, qs.pmax, qs.ra, qs.rb, sink, lo, pl, pr);
+    const u32 lane = lane_id();
+    const u32 mx = __reduce_max_sync(0xffffffffu, qs.cnt);
+    u32 ca = 0, cb = 0;
+    for (u32 j = 0; j < qs.cnt; ++j) {
+        const ct c = C::make(q.k[qs.cq][j * 32 + lane], q.i[qs.cq][j * 32 + lane]);
+        ca += (u32)(c >= lo && c < pl);
+        cb += (u32)(c >= pl && c <= pr);
+    }
+    ca = __reduce_add_sync(0xffffffffu, ca);
+    cb = __reduce_add_sync(0xffffffffu, cb);
+    u64 ra = 0, rb = 0;
+    if (lane == 0) {
+        if (ca) ra = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ca);
+        if (cb) rb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)cb);
+    }
+    qs.ra = ra;
+    qs.rb = rb;
+    qs.pcnt = qs.cnt;
+    qs.pmax = mx;
+    qs.cq ^= 1u;
+    qs.cnt = 0;
+    __syncwarp();
+}
+
+template <int DT>
+__device__ __forceinline__ void lq_drain(WarpQ<Key<DT>::KW>& q, LQState& qs, const Sink<DT>& sink,
+                                         typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
+                                         typename Comp<Key<DT>::KW>::t pr) {
+    if (__any_sync(0xffffffffu, qs.cnt)) lq_flush<DT>(q, qs, sink, lo, pl, pr);
+    if (qs.pmax) lq_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pcnt, qs.pmax, qs.ra, qs.rb, sink, lo, pl, pr);
+    qs.pmax = 0;
+    __syncwarp();
+}
+
+// Each lane appends its own hits (bit q of `hit`: slot q; key_at(q) and
+// pos(q) for a lane-dependent q) to its part of the active buffer; a flush
+// first when some lane's part would overflow.  All 32 lanes call.
+template <int DT, class PosF, class KeyAt>
+__device__ __forceinline__ void lq_append(u32 hit, PosF pos, KeyAt key_at, typename Comp<Key<DT>::KW>::t lo,
+                                          typename Comp<Key<DT>::KW>::t pl, typename Comp<Key<DT>::KW>::t pr,
+                                          const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, LQState& qs) {
+    constexpr u32 PER_LANE = LQ<Key<DT>::KW>::PER_LANE, CH = LQ<Key<DT>::KW>::CH;
+    if (!__any_sync(0xffffffffu, hit)) return;
+    const u32 lane = lane_id();
+    if (__any_sync(0xffffffffu, qs.cnt + (u32)__popc(hit) > PER_LANE)) {
+        // slow path: chunks of CH slots in turn (at most CH hits each, which
+        // always fit a lane once its part is flushed)
+#pragma unroll 1
+        for (u32 h = 0; h < 16 / CH; ++h) {
+            u32 m = (hit >> (CH * h)) & ((1u << CH) - 1u);
+            if (__any_sync(0xffffffffu, qs.cnt + (u32)__popc(m) > PER_LANE)) lq_flush<DT>(q, qs, sink, lo, pl, pr);
+            while (m) {
+                const u32 sq = CH * h + (u32)(__ffs(m) - 1);
+                m &= m - 1;
+                q.k[qs.cq][qs.cnt * 32 + lane] = key_at(sq);
+                q.i[qs.cq][qs.cnt * 32 + lane] = pos((int)sq);
+                ++qs.cnt;
+            }
+        }
+        return;
+    }
+    u32 m = hit;
+    while (m) {
+        const u32 sq = (u32)(__ffs(m) - 1);
+        m &= m - 1;
+        q.k[qs.cq][qs.cnt * 32 + lane] = key_at(sq);
+        q.i[qs.cq][qs.cnt * 32 + lane] = pos((int)sq);
+        ++qs.cnt;
+    }
+}
 // r[q] for a lane-dependent q without dynamic register indexing (which would
 // move r to local memory): a tree of selects.
 template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) {

@@ -175,7 +175,7 @@ __device__ void tma_consume_sparse(const SelArgs& a, const SelState& s, const un
     const ct lo = C::from128(s.lo), pl = C::from128(s.pl), pr = C::from128(s.pr);
     const u32 lane = lane_id();
     const InputSrc<DT> isrc = InputSrc<DT>::make(a.keys, s.m_src); // head = 0: input is 16-byte aligned
-    QState qs = QState::make();
+    LQState qs = LQState::make();
     const TileBounds<DT> tbd = TileBounds<DT>::make(pl, pr);
     for (u64 i = 0; i < my_n; ++i) {
         const u32 stg = (u32)(i % Cfg::STAGES);
@@ -208,9 +208,13 @@ __device__ void tma_consume_sparse(const SelArgs& a, const SelState& s, const un
 #pragma unroll
             for (int q = 0; q < 16; ++q) rr[q] = 0;
         }
+        // the hits' keys come from the stage, which is released after them
+        const unsigned char* mine = stages + (size_t)stg * Cfg::BYTES + threadIdx.x * 16u;
+        lq_append<DT>(hit, pos, [&](u32 sq) {
+            return K::fwd(*reinterpret_cast<const raw_t*>(mine + (sq / EPV) * (TMA_CONS * 16u) + (sq % EPV) * sizeof(raw_t)));
+        }, lo, pl, pr, sink, wq, qs);
         __syncwarp();
-        if (ok && lane == 0) mbar_arrive(&empty[stg]); // keys are in registers: the stage may be refilled
-        sparse_append_hits<DT>(hit, pos, [&](u32 sq) { return K::fwd(pick16(rr, sq)); }, lo, pl, pr, sink, wq, qs);
+        if (ok && lane == 0) mbar_arrive(&empty[stg]); // the stage may be refilled
     }
     // the ragged last tile, read directly by the block that owns it
     const u64 nfull = s.m_src / Cfg::TILE;
@@ -220,9 +224,12 @@ __device__ void tma_consume_sparse(const SelArgs& a, const SelState& s, const un
         const u64 tb = nfull * (u64)Cfg::TILE;
         const u32 valid = isrc.template load16<TMA_CONS>(tb, kk, ii);
         auto pos = [&](int q) -> u32 { return isrc.template idx_of<TMA_CONS>(tb, q); };
-        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, wq, qs);
+        u32 tail_hit = 0;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) tail_hit |= (u32)(C::make(kk[q], pos(q)) <= pr) << q;
+        lq_append<DT>(tail_hit & valid, pos, [&](u32 sq) { return pick16(kk, sq); }, lo, pl, pr, sink, wq, qs);
     }
-    queue_drain<DT>(wq, qs, sink, lo, pl, pr);
+    lq_drain<DT>(wq, qs, sink, lo, pl, pr);
 }
 
 // Dense first level (many elements in a; the window starts at the smallest

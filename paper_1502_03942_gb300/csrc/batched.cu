@@ -466,12 +466,12 @@ template <int DT> __global__ void __launch_bounds__(WIDE_NT, 2) k_wide_pass(Batc
         }
         return;
     }
-    // consumers: the hits (pair <= pr) go to the warp's queue, classified
-    // and reserved in batches (select_core.cuh), drained when the warp
-    // leaves the row
+    // consumers: the hits (pair <= pr) go to the warp's per-lane queue,
+    // classified and reserved in batches (select_core.cuh), drained when the
+    // warp leaves the row
     const u32 lane = lane_id();
     WarpQ<KW>& wq = wqs[threadIdx.x >> 5];
-    QState qs = QState::make();
+    LQState qs = LQState::make();
     const ct lo0 = 0;
     WideRow<DT> w;
     w.row = 0xFFFFFFFFu;
@@ -491,7 +491,7 @@ template <int DT> __global__ void __launch_bounds__(WIDE_NT, 2) k_wide_pass(Batc
         if (!ok) continue; // timed out: latched; the remaining waits return at once
         const WideMeta m = meta[stg];
         if (m.j != j_cur) { // a new row: this warp leaves the previous one
-            if (w.live) queue_drain<DT>(wq, qs, w.sink, lo0, w.pl, w.pr);
+            if (w.live) lq_drain<DT>(wq, qs, w.sink, lo0, w.pl, w.pr);
             __syncwarp();
             if (lane == 0 && j_cur != 0xFFFFFFFFu) wide_row_close<DT>(b, w, ndone, WIDE_CONS / 32);
             ndone = 0;
@@ -550,14 +550,14 @@ template <int DT> __global__ void __launch_bounds__(WIDE_NT, 2) k_wide_pass(Batc
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[stg]); // keys are in registers
-            sparse_append_hits<DT>(hit, pos, [&](u32 sq) { return pick16(kk, sq); }, lo0, w.pl, w.pr, w.sink, wq, qs);
+            lq_append<DT>(hit, pos, [&](u32 sq) { return pick16(kk, sq); }, lo0, w.pl, w.pr, w.sink, wq, qs);
             ++ndone;
         } else {
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[stg]);
         }
     }
-    if (w.live) queue_drain<DT>(wq, qs, w.sink, lo0, w.pl, w.pr);
+    if (w.live) lq_drain<DT>(wq, qs, w.sink, lo0, w.pl, w.pr);
     __syncwarp();
     if (lane == 0 && j_cur != 0xFFFFFFFFu) wide_row_close<DT>(b, w, ndone, WIDE_CONS / 32);
 }

@@ -700,90 +700,6 @@ template <int KW> struct WarpQ {
     u32 i[2][QCAP];
 };
 
-// Per-warp queue state (uniform across the warp).
-struct QState {
-    u32 nq;     // entries in the active buffer
-    u32 cq;     // active buffer
-    u32 pn;     // entries in the other buffer still to be written (0: none)
-    u64 ra, rb; // lane 0: reservations of those entries (atomics in flight)
-    __device__ static QState make() { return QState{0u, 0u, 0u, 0ull, 0ull}; }
-};
-
-// Writes the n entries of one buffer, whose classes were counted when it was
-// queued, from the reservations ra / rb (lane 0's values).
-template <int DT>
-__device__ __forceinline__ void queue_write(const typename Comp<Key<DT>::KW>::key_t* qk, const u32* qi, u32 n,
-                                            u64 ra, u64 rb, const Sink<DT>& sink,
-                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
-                                            typename Comp<Key<DT>::KW>::t pr) {
-    typedef Comp<Key<DT>::KW> C;
-    typedef typename C::t ct;
-    u64 ba = __shfl_sync(0xffffffffu, (unsigned long long)ra, 0);
-    u64 bb = __shfl_sync(0xffffffffu, (unsigned long long)rb, 0);
-    const u32 below = lanemask_lt();
-    for (u32 e0 = 0; e0 < n; e0 += 32) {
-        const u32 e = e0 + lane_id();
-        bool isa = false, isb = false;
-        typename C::key_t kv = 0;
-        u32 iv = 0;
-        if (e < n) {
-            kv = qk[e];
-            iv = qi[e];
-            const ct c = C::make(kv, iv);
-            isa = c >= lo && c < pl;
-            isb = c >= pl && c <= pr;
-        }
-        const u32 bala = __ballot_sync(0xffffffffu, isa), balb = __ballot_sync(0xffffffffu, isb);
-        if (isa) sink.put_a(ba + __popc(bala & below), kv, iv);
-        if (isb) sink.put_b(bb + __popc(balb & below), kv, iv);
-        ba += __popc(bala);
-        bb += __popc(balb);
-    }
-}
-
-// Writes the pending buffer (if any), then counts the classes of the active
-// one, issues its reservations without waiting for them, and switches
-// buffers.  All 32 lanes call.
-template <int DT>
-__device__ __forceinline__ void queue_flush(WarpQ<Key<DT>::KW>& q, QState& qs, const Sink<DT>& sink,
-                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
-                                            typename Comp<Key<DT>::KW>::t pr) {
-    typedef Comp<Key<DT>::KW> C;
-    typedef typename C::t ct;
-    __syncwarp();
-    if (qs.pn) queue_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pn, qs.ra, qs.rb, sink, lo, pl, pr);
-    u32 ca = 0, cb = 0;
-    for (u32 e = lane_id(); e < qs.nq; e += 32) {
-        const ct c = C::make(q.k[qs.cq][e], q.i[qs.cq][e]);
-        ca += (u32)(c >= lo && c < pl);
-        cb += (u32)(c >= pl && c <= pr);
-    }
-    ca = __reduce_add_sync(0xffffffffu, ca);
-    cb = __reduce_add_sync(0xffffffffu, cb);
-    u64 ra = 0, rb = 0;
-    if (lane_id() == 0) {
-        if (ca) ra = atomicAdd((unsigned long long*)sink.cnt_a, (unsigned long long)ca);
-        if (cb) rb = atomicAdd((unsigned long long*)sink.cnt_b, (unsigned long long)cb);
-    }
-    qs.ra = ra;
-    qs.rb = rb;
-    qs.pn = qs.nq;
-    qs.cq ^= 1u;
-    qs.nq = 0;
-    __syncwarp();
-}
-
-// End of the pass: everything queued is written.
-template <int DT>
-__device__ __forceinline__ void queue_drain(WarpQ<Key<DT>::KW>& q, QState& qs, const Sink<DT>& sink,
-                                            typename Comp<Key<DT>::KW>::t lo, typename Comp<Key<DT>::KW>::t pl,
-                                            typename Comp<Key<DT>::KW>::t pr) {
-    if (qs.nq) queue_flush<DT>(q, qs, sink, lo, pl, pr);
-    if (qs.pn) queue_write<DT>(q.k[qs.cq ^ 1u], q.i[qs.cq ^ 1u], qs.pn, qs.ra, qs.rb, sink, lo, pl, pr);
-    qs.pn = 0;
-    __syncwarp();
-}
-
 // ---- per-lane warp queues.  Lane L's j-th entry sits at index j * 32 + L
 // of a buffer, so a lane appends its own hits with no cross-lane step (no
 // scan) and without bank conflicts; the lanes' counts differ, so flushing and
@@ -923,75 +839,6 @@ template <class T> __device__ __forceinline__ T pick16(const T (&r)[16], u32 q) 
     return (q & 8u) ? l3[1] : l3[0];
 }
 
-// One tile in sparse mode (all 32 lanes call; no block-wide barrier).  Every
-// element with pair <= pr (the only ones that can be in a or b) is queued.
-// Hits are rare, so each lane appends its own at an offset from one warp
-// scan (the per-chunk counts packed in one word) and visits only its set
-// bits.  The 16 slots go in chunks of CH slots, at most CH * 32 <= QCAP hits
-// each, in turn, so one flush always makes room; the chunks share one copy
-// of the code.  pos(q) must accept a lane-dependent q.
-template <int DT, class CT, class KeyT, class PosF>
-__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, u32 valid, CT lo, CT pl, CT pr,
-                                                const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
-    classify_sparse<DT>(kk, pos, [&](u32 sq) { return pick16(kk, sq); }, valid, lo, pl, pr, sink, q, qs);
-}
-
-// The appending step alone, for a hit mask computed by the caller (bit q:
-// slot q's pair is at most pr); key_at(q) gives slot q's key image for a
-// lane-dependent q.
-template <int DT, class CT, class PosF, class KeyAt>
-__device__ __forceinline__ void sparse_append_hits(u32 hit, PosF pos, KeyAt key_at, CT lo, CT pl, CT pr,
-                                                   const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q, QState& qs) {
-    constexpr u32 QCAP = (u32)WarpQ<Key<DT>::KW>::QCAP;
-    constexpr u32 CH = QCAP >= 8 * 32 ? 8 : 4;    // slots per chunk
-    constexpr u32 NCH = 16 / CH;                  // chunks per tile
-    constexpr u32 FB = 32 / NCH;                  // bits per packed chunk count
-    static_assert(CH * 32 <= QCAP, "queue too small for a chunk");
-    static_assert(CH * 32 < (1u << FB), "chunk count does not fit its field");
-    if (!__any_sync(0xffffffffu, hit)) return;
-    u32 cnt = 0;
-#pragma unroll
-    for (u32 h = 0; h < NCH; ++h) cnt |= (u32)__popc((hit >> (CH * h)) & ((1u << CH) - 1)) << (FB * h);
-    u32 incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const u32 y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane_id() >= (u32)o) incl += y;
-    }
-    const u32 tot = __shfl_sync(0xffffffffu, incl, 31);
-    const u32 excl = incl - cnt;
-    constexpr u32 FMASK = FB == 32 ? 0xFFFFFFFFu : (1u << FB) - 1;
-#pragma unroll 1
-    for (u32 h = 0; h < NCH; ++h) {
-        const u32 th = (tot >> (FB * h)) & FMASK;
-        if (th == 0) continue;
-        if (qs.nq + th > QCAP) queue_flush<DT>(q, qs, sink, lo, pl, pr);
-        u32 slot = qs.nq + ((excl >> (FB * h)) & FMASK);
-        u32 m = (hit >> (CH * h)) & ((1u << CH) - 1);
-        while (m) {
-            const u32 sq = CH * h + (u32)(__ffs(m) - 1);
-            m &= m - 1;
-            q.k[qs.cq][slot] = key_at(sq);
-            q.i[qs.cq][slot] = pos((int)sq);
-            ++slot;
-        }
-        qs.nq += th;
-    }
-}
-
-// The same, with key_at(q) giving slot q's key for a lane-dependent q (for
-// instance from a shared-memory stage instead of a tree of selects).
-template <int DT, class CT, class KeyT, class PosF, class KeyAt>
-__device__ __forceinline__ void classify_sparse(const KeyT (&kk)[16], PosF pos, KeyAt key_at, u32 valid, CT lo,
-                                                CT pl, CT pr, const Sink<DT>& sink, WarpQ<Key<DT>::KW>& q,
-                                                QState& qs) {
-    typedef Comp<Key<DT>::KW> C;
-    u32 hit = 0;
-#pragma unroll
-    for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
-    sparse_append_hits<DT>(hit & valid, pos, key_at, lo, pl, pr, sink, q, qs);
-}
-
 // Register path in sparse mode.
 template <int NT, int DT, class Src>
 __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, typename Comp<Src::KW>::t lo,
@@ -999,8 +846,9 @@ __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, type
                                   WarpQ<Key<DT>::KW>& q) {
     typedef typename Src::key_t key_t;
     constexpr u64 TILE = (u64)NT * 16;
+    typedef Comp<Src::KW> C;
     const u64 ntiles = (src.extent() + TILE - 1) / TILE;
-    QState qs = QState::make();
+    LQState qs = LQState::make();
     for (u64 t = tile0; t < ntiles; t += tile_step) {
         key_t kk[16];
         u32 ii[16];
@@ -1010,9 +858,12 @@ __device__ void pass_tiles_sparse(const Src& src, u64 tile0, u64 tile_step, type
             if constexpr (Src::IMPLICIT_IDX) return src.template idx_of<NT>(tb, s);
             else return pick16(ii, (u32)s);
         };
-        classify_sparse<DT>(kk, pos, valid, lo, pl, pr, sink, q, qs);
+        u32 hit = 0;
+#pragma unroll
+        for (int s = 0; s < 16; ++s) hit |= (u32)(C::make(kk[s], pos(s)) <= pr) << s;
+        lq_append<DT>(hit & valid, pos, [&](u32 sq) { return pick16(kk, sq); }, lo, pl, pr, sink, q, qs);
     }
-    queue_drain<DT>(q, qs, sink, lo, pl, pr);
+    lq_drain<DT>(q, qs, sink, lo, pl, pr);
 }
 
 // Register path: every thread loads its 16 elements of each tile itself.

@@ -336,13 +336,14 @@ topk_status topk_frequent(topk_ctx *ctx, const void *d_objects, uint64_t n, topk
 
 /* Autotuner of topk_select_batched (no counterpart in the paper): runs the
  * given batch with every candidate block size (256, 512, 1024 threads),
- * sample size (1024, 2048, 4096) and finish threshold (the block's capacity
- * and half of it), then with the fastest of those and every split length of
- * 2^13, 2^15, 2^17 and none, times each with CUDA events on `stream` (best
- * of three after one warm-up), and remembers the fastest for this dtype and
- * row-count bucket (floor(log2(rows))) in the context.  Arguments as
- * topk_select_batched; every output is overwritten many times (the last run
- * uses the chosen setting, so the outputs are that call's result).
+ * sample size (512, 1024, 2048, 4096) and finish threshold (the block's
+ * capacity and half of it), then with the fastest of those and every split
+ * length of 2^13, 2^15, 2^17 and none, times each with CUDA events on
+ * `stream` (best of three after one warm-up), and remembers the fastest for
+ * this dtype and row-count bucket (floor(log2(rows))) in the context.
+ * Arguments as topk_select_batched; every output is overwritten many times
+ * (the last run uses the chosen setting, so the outputs are that call's
+ * result).
  *   base   NULL or settings copied into every candidate (seed, partitions,
  *          delta_factor, flags).
  *   best   NULL or receives the chosen settings.

@@ -961,7 +961,7 @@ extern "C" topk_status topk_tune_batched(topk_ctx* ctx, const void* d_keys, cons
     bool have = false;
     for (u32 threads : {256u, 512u, 1024u}) {
         const u32 cap = threads == 1024 ? full : threads == 512 ? full / 2 : full / 4;
-        for (u32 sample : {1024u, 2048u, 4096u}) {
+        for (u32 sample : {512u, 1024u, 2048u, 4096u}) {
             for (u32 T : {cap, cap / 2}) {
                 topk_params p = b0;
                 p.block_threads = threads;

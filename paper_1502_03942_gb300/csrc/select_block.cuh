@@ -1,8 +1,8 @@
 // select_block.cuh — one thread block runs whole recursion levels of the
 // selection: planning (sample + pivots), a block-wide pass, the branch, and
 // the final exact selection among at most T candidates.  Used by the
-// single-selection kernels (select.cu: k_plan, k_finish) and by the batched
-// kernel (batched.cu), where every block selects whole rows.
+// single-selection finish (select_impl.cuh: k_finish) and by the batched
+// kernels (batched.cu), where every block selects whole rows.
 #pragma once
 
 #include "select_core.cuh"

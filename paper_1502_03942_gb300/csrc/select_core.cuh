@@ -1,6 +1,6 @@
 // select_core.cuh — the steps of sample-based selection as block-level device
-// functions, shared by the single-selection kernels (select.cu) and the
-// batched kernel (batched.cu).
+// functions, shared by the single-selection kernels (select_impl.cuh) and the
+// batched kernels (batched.cu).
 //
 // One recursion level of Algorithm "select" (paper, Section 2) is
 //   pickPivots : draw a sample of the undecided elements, take the sample

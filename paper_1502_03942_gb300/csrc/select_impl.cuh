@@ -4,9 +4,10 @@
 // Launch sequence of one call (all on the caller's stream, no host round
 // trip), per recursion level:
 //   k_sample (grid)     per-partition draws of the current window -> sample
-//                       array + histogram over the window
-//   k_pivots (1 block)  pivots = sample elements of ranks k|S|/n -/+ Delta,
-//                       read off the histogram and refined in two bins
+//                       array (draw j at slot j)
+//   k_pivots (1 block)  pivots = sample elements of ranks k|S|/n -/+ Delta:
+//                       the sample into shared memory, one histogram over
+//                       its range, the two rank bins ranked exactly
 //   k_pass   (grid)     one read of the source: a -> output, b -> candidate
 //                       buffer; the last block takes the branch
 // then k_finish (1 block): remaining levels inside one block until at most T
@@ -444,7 +445,7 @@ __global__ void __launch_bounds__(TMA_NT, (TmaCfg<DT, DENSE>::MIN_BLOCKS)) k_pas
     grid_dep_wait();
     const SelState s = *a.st;
     if (s.phase != PH_RUN || !s.pending || s.src != SRC_INPUT || (s.dense != 0) != DENSE) {
-        grid_dep_release(); // the variant not needed lets the next launch proceed at once
+        grid_dep_release(); // nothing to do (an earlier failure, or the other mode): the next launch proceeds
         return;
     }
     // the tile thresholds of the dense variant assume a window starting at the
